@@ -154,7 +154,8 @@ static int tmpl_build(tmpl_t *t, int k, const int32_t *edges)
  * edge {a, b}.  Backtracking over vertices in BFS order from vertex 0; every
  * tree edge joins a vertex to its BFS parent, so checking each vertex against
  * its parent checks every edge, and an injective edge map of a finite edge set
- * into itself is onto.
+ * into itself is onto.  Each automorphism is enumerated, so the cost grows
+ * with |Aut(T)| (fine for the workload templates; a k-star has (k-1)!).
  */
 static int is_adj(const tmpl_t *t, int a, int b)
 {
