@@ -1,0 +1,254 @@
+/*
+ * cc.h -- C ABI of the GB300 colour-coding tree counter.
+ *
+ * Method: arXiv 1804.09764 ("High-Performance Massive Subgraph Counting using
+ * Pipelined Adaptive-Group Communication"), Section 2.1.  For a tree template
+ * T on k vertices and a graph G, each colouring j assigns every vertex a colour
+ * in [0, k) (Algorithm 1), and the dynamic program of Eq. 1 counts colourful
+ * embeddings bottom-up over the partition tree of T; Eq. 3 scales the count by
+ * k^k / k! into an estimate of the number of non-induced copies of T in G
+ * (Section 2, "Subgraph-counting problem").
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a cc_status: CC_OK (0), CC_PENDING (1, serving only)
+ *     or a negative error.  On error, cc_last_error() returns a message for the
+ *     calling thread; outputs are left unspecified.
+ *   - The library copies every input it keeps; caller buffers may be freed as
+ *     soon as a call returns.  Outputs go only into caller-owned buffers.
+ *   - Handles (graphs, templates, requests) are owned by their context and die
+ *     with it.
+ *   - Wide integers are arrays of 64-bit limbs, least significant first.
+ *   - All device work runs in this library's CUDA kernels on one GPU; there is
+ *     no CPU fallback.
+ *   - A context may be used from several threads; calls are serialised on an
+ *     internal lock (the serving loop runs on its own thread).
+ */
+#ifndef CC_H
+#define CC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cc_status;
+
+#define CC_OK                0
+#define CC_PENDING           1   /* serving: request not finished yet */
+#define CC_ERR_INVALID_ARG  -1   /* null pointer, bad size, bad option */
+#define CC_ERR_BAD_GRAPH    -2   /* self-loop, duplicate, asymmetric edge, index out of range */
+#define CC_ERR_NOT_TREE     -3   /* template edges do not form a tree on 0..k-1 */
+#define CC_ERR_K_RANGE      -4   /* k outside 1..16 */
+#define CC_ERR_BUDGET       -5   /* the plan does not fit the HBM budget */
+#define CC_ERR_WIDTH        -6   /* exact counts would need more than 256 bits */
+#define CC_ERR_CUDA         -7   /* a CUDA call failed (message names it) */
+#define CC_ERR_TIMEOUT      -8   /* a wait ran out of time */
+#define CC_ERR_CANCELLED    -9   /* request was cancelled */
+#define CC_ERR_NOT_FOUND   -10   /* unknown handle */
+#define CC_ERR_CAPACITY    -11   /* caller buffer too small (needed size reported) */
+#define CC_ERR_NO_MEMORY   -12   /* host allocation failed */
+#define CC_ERR_INTERNAL    -13
+
+typedef struct cc_ctx cc_ctx;
+typedef int64_t cc_graph_id;
+typedef int64_t cc_template_id;
+typedef int64_t cc_req_id;
+
+/* Context options.  Call cc_default_options() first, then change fields. */
+typedef struct cc_options {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t width_bits;        /* 0: exact counts, integer width chosen per table from a
+                                  homomorphism bound; 64/128/192/256: every table at this
+                                  width, counts returned as residues mod 2^width_bits */
+    void *stream;              /* cudaStream_t for cc_count; NULL: the library makes one */
+    void *arena;               /* caller-owned device memory that holds every library
+                                  buffer (graphs, tables, scratch); NULL: the library
+                                  allocates hbm_budget_bytes itself */
+    uint64_t hbm_budget_bytes; /* size of arena; with arena == NULL, 0 means 90% of the
+                                  device memory free at cc_create */
+    int32_t split_threshold;   /* neighbour-list task size s (Algorithm 4); 0: default 1024 */
+    int32_t batch;             /* colourings processed together in one pass; 0: largest
+                                  that fits the budget, at most 16 */
+    int32_t block_vertices;    /* vertices per streamed block; 0: largest that fits */
+    int32_t use_cuda_graph;    /* 1: capture the per-batch schedule once and replay it */
+    int32_t fused;             /* 1: fused gather+combine kernel for low-degree vertices */
+    int32_t autotune;          /* 1: time candidate launch shapes on first use of a plan */
+    int32_t max_slots;         /* serving: requests in flight at once (default 4) */
+    int32_t timing;            /* 1: record per-kernel CUDA-event times (cc_kernel_stats) */
+    int32_t reserved[6];
+} cc_options;
+
+void cc_default_options(cc_options *opt);
+
+/* Create a context on opt->device.  *out receives the handle. */
+cc_status cc_create(cc_ctx **out, const cc_options *opt);
+cc_status cc_destroy(cc_ctx *ctx);
+
+/* Thread-local message of the last failing call; never NULL. */
+const char *cc_last_error(void);
+const char *cc_status_string(cc_status s);
+
+#define CC_VALIDATE 1u   /* check symmetry, duplicates, self-loops, index range (host, O(m log m)) */
+
+/*
+ * Load an undirected graph G(V, E) (Section 2) in CSR form.
+ *   n           number of vertices, 0 <= n < 2^31
+ *   row_ptr     [n+1] int64 offsets, row_ptr[0] = 0, non-decreasing
+ *   col_idx     [row_ptr[n]] int32 neighbour ids; both directions of every
+ *               edge must be present; N(v) must not contain v
+ *   Pointers may be host or device memory (detected); the library copies.
+ *   flags       CC_VALIDATE to check the conditions above (CC_ERR_BAD_GRAPH)
+ * The device copy drops isolated vertices from the table domain (they belong
+ * to no embedding of a template with k >= 2) and lives in the arena.
+ */
+cc_status cc_graph_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr,
+                            const int32_t *col_idx, uint32_t flags, cc_graph_id *out);
+cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g);
+
+/*
+ * Load a tree template T (Section 2.1), k = |V_T| in 1..16.
+ *   edges  [2*(k-1)] int32 vertex pairs on 0..k-1
+ *   root   root rho(T) of the partition (any vertex gives the same counts,
+ *          Section 2.1: the root "can be picked arbitrarily"); -1: the planner
+ *          picks the root with the lowest modelled cost
+ */
+cc_status cc_template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, int32_t root,
+                           cc_template_id *out);
+cc_status cc_template_free(cc_ctx *ctx, cc_template_id t);
+
+/* Results of a count (one per call or per request). */
+typedef struct cc_result {
+    int32_t k;
+    int32_t limbs;          /* 64-bit limbs per count needed/written */
+    int32_t exact;          /* 1: counts are exact colourful copies (maps / |Aut T|);
+                               0: residues of labelled maps mod 2^(64*limbs) */
+    int32_t n_iter;
+    int64_t aut;            /* |Aut(T)| */
+    int32_t root;           /* partition root used */
+    int32_t batch;          /* colourings per pass used */
+    double estimate;        /* mean over colourings of copies_j * k^k / k! (Eq. 3); exact mode */
+    double median_of_means; /* Algorithm 1's final step over t groups; exact mode */
+    double device_seconds;  /* GPU time of the colourings (CUDA events) */
+    double wall_seconds;    /* host wall time of the call / request latency */
+    uint64_t workspace_bytes; /* device bytes the plan used (tables + scratch) */
+    int64_t kernel_launches;  /* kernels launched for this call */
+} cc_result;
+
+/*
+ * Run colourings 0..n_iter-1 from `seed` (Algorithm 1's outer loop).
+ *   counts  [n_iter][limbs_capacity] uint64, host memory: per-colouring
+ *           colourful copies (exact mode) or map residues (forced width)
+ *   limbs_capacity must be >= res->limbs (CC_ERR_CAPACITY otherwise; res->limbs
+ *           then says how many are needed)
+ *   res     optional (may be NULL)
+ * Colour of vertex v in colouring j: h = F(F(F(seed) + j) + v),
+ * col = floor(h * k / 2^64), F = SplitMix64 output function of state x + 0x9E3779B97F4A7C15.
+ */
+cc_status cc_count(cc_ctx *ctx, cc_graph_id g, cc_template_id t, uint64_t seed, int32_t n_iter,
+                   uint64_t *counts, int32_t limbs_capacity, cc_result *res);
+
+/* Extended arguments for cc_count_ex. */
+typedef struct cc_count_args {
+    uint64_t seed;
+    int64_t first_iter;              /* index j of the first colouring */
+    int32_t n_iter;
+    int32_t mom_groups;              /* t for the median of means (0 -> 1) */
+    int32_t width_bits;              /* -1: context default; otherwise as cc_options.width_bits */
+    int32_t reserved0;
+    const int64_t *sample_vertices;  /* optional host [n_sample] original vertex ids */
+    int64_t n_sample;
+    uint64_t *sample_maps;           /* optional host [n_iter][n_sample][limbs_capacity]:
+                                        M(v, T, all colours) = labelled colourful maps with the
+                                        root on v, mod 2^(64*limbs) */
+    uint64_t *maps;                  /* optional host [n_iter][limbs_capacity]: labelled maps
+                                        (sum over v, before the division by |Aut T|) */
+} cc_count_args;
+
+cc_status cc_count_ex(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_count_args *args,
+                      uint64_t *counts, int32_t limbs_capacity, cc_result *res);
+
+/* Static description of the plan for (graph, template) under the context options. */
+typedef struct cc_plan_info {
+    int32_t k, root, n_chains, n_tables;
+    int32_t limbs_root;              /* width of the root chain in 64-bit limbs */
+    int32_t batch;                   /* colourings per pass */
+    int64_t n_vertices, n_active, n_directed_edges;
+    int64_t n_blocks;                /* vertex blocks per chain */
+    double updates_per_colouring;    /* sum over gathered non-leaf passive tables of 2m*C(k,p) */
+    double gather_bytes_per_colouring;   /* algorithmic bytes of the table gathers */
+    double algorithmic_bytes_per_colouring; /* gathers + table writes + CSR + leaf colour reads */
+    double pairs_per_colouring;      /* combine multiply-adds per colouring */
+    uint64_t workspace_bytes;
+    int64_t table4_memory, table4_computation;  /* Table 4 cost numbers of the partition */
+} cc_plan_info;
+
+cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out);
+
+/* Per-kernel CUDA-event statistics (opt.timing = 1); cumulative since reset. */
+#define CC_KERNEL_KINDS 8
+typedef struct cc_kernel_stats {
+    const char *name[CC_KERNEL_KINDS];
+    int64_t launches[CC_KERNEL_KINDS];
+    double seconds[CC_KERNEL_KINDS];   /* summed event durations */
+    double bytes[CC_KERNEL_KINDS];     /* algorithmic bytes moved */
+    int64_t total_launches;            /* every kernel launched by the library */
+} cc_kernel_stats;
+
+cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out);
+cc_status cc_kernel_stats_reset(cc_ctx *ctx);
+
+/* ------------------------------------------------------------------ serving */
+
+/* One count request (same arithmetic as cc_count_ex). */
+typedef struct cc_request {
+    cc_graph_id graph;
+    cc_template_id tmpl;
+    uint64_t seed;
+    int64_t first_iter;
+    int32_t n_iter;
+    int32_t priority;       /* reserved */
+} cc_request;
+
+/*
+ * Submit a request to the continuous-batching loop.  It is admitted when a
+ * slot is free and its plan's workspace fits the free arena; admitted requests
+ * run concurrently on their own streams, one colouring batch at a time.
+ */
+cc_status cc_submit(cc_ctx *ctx, const cc_request *req, cc_req_id *out);
+/* CC_PENDING while running; CC_OK with results; an error if it failed.
+ * counts as for cc_count.  A finished request is forgotten after a successful
+ * poll/wait that returns its results. */
+cc_status cc_poll(cc_ctx *ctx, cc_req_id id, cc_result *res, uint64_t *counts, int32_t limbs_capacity);
+cc_status cc_wait(cc_ctx *ctx, cc_req_id id, int64_t timeout_ns, cc_result *res, uint64_t *counts,
+                  int32_t limbs_capacity);
+cc_status cc_cancel(cc_ctx *ctx, cc_req_id id);
+
+typedef struct cc_serve_stats {
+    int64_t submitted, completed, failed, cancelled, in_flight, queued;
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+    double busy_seconds;           /* wall time with at least one request in flight */
+    int64_t admissions_deferred;   /* times a queued request waited for memory or a slot */
+} cc_serve_stats;
+
+cc_status cc_serve_stats_get(cc_ctx *ctx, cc_serve_stats *out);
+
+/* ------------------------------------------------------------------ helpers */
+
+/* Table 4 cost numbers of the partition of a template from a given root with
+ * children attached largest subtree first (order = 0) or by the planner's own
+ * order (order = 1).  Host only. */
+cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_t order,
+                           int64_t *memory, int64_t *computation);
+
+/* |Aut(T)| from rooted canonical forms at the tree centre.  Host only. */
+cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *aut);
+
+/* Library version string. */
+const char *cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H */

@@ -284,7 +284,6 @@ static void root_tree(dp_t *d, int x, int parent)
  */
 static u256 *subtree_table(dp_t *d, int x)
 {
-    const int k = d->t.k;
     /* base case: M(v, {x}, {c}) = [col(v) == c] */
     u256 *cur = table_alloc(d, 1);
     if (!cur) return NULL;

@@ -1,0 +1,362 @@
+// api.cpp -- the extern "C" entry points declared in include/cc.h.
+#include <cstring>
+
+#include "runtime.h"
+
+namespace cc {
+
+static thread_local std::string t_err = "no error";
+
+cc_status fail(cc_status s, const std::string &msg)
+{
+    t_err = msg;
+    return s;
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" {
+
+const char *cc_version(void) { return "cc-gb300 0.1 (sm_103a)"; }
+
+const char *cc_last_error(void) { return t_err.c_str(); }
+
+const char *cc_status_string(cc_status s)
+{
+    switch (s) {
+    case CC_OK: return "CC_OK";
+    case CC_PENDING: return "CC_PENDING";
+    case CC_ERR_INVALID_ARG: return "CC_ERR_INVALID_ARG";
+    case CC_ERR_BAD_GRAPH: return "CC_ERR_BAD_GRAPH";
+    case CC_ERR_NOT_TREE: return "CC_ERR_NOT_TREE";
+    case CC_ERR_K_RANGE: return "CC_ERR_K_RANGE";
+    case CC_ERR_BUDGET: return "CC_ERR_BUDGET";
+    case CC_ERR_WIDTH: return "CC_ERR_WIDTH";
+    case CC_ERR_CUDA: return "CC_ERR_CUDA";
+    case CC_ERR_TIMEOUT: return "CC_ERR_TIMEOUT";
+    case CC_ERR_CANCELLED: return "CC_ERR_CANCELLED";
+    case CC_ERR_NOT_FOUND: return "CC_ERR_NOT_FOUND";
+    case CC_ERR_CAPACITY: return "CC_ERR_CAPACITY";
+    case CC_ERR_NO_MEMORY: return "CC_ERR_NO_MEMORY";
+    case CC_ERR_INTERNAL: return "CC_ERR_INTERNAL";
+    default: return "CC_UNKNOWN_STATUS";
+    }
+}
+
+void cc_default_options(cc_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->device = 0;
+    opt->width_bits = 0;
+    opt->split_threshold = 0;
+    opt->batch = 0;
+    opt->block_vertices = 0;
+    opt->use_cuda_graph = 0;
+    opt->fused = 0;
+    opt->autotune = 0;
+    opt->max_slots = 4;
+    opt->timing = 0;
+}
+
+cc_status cc_create(cc_ctx **out, const cc_options *opt)
+{
+    if (!out) return fail(CC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto c = new (std::nothrow) Ctx();
+    if (!c) return fail(CC_ERR_NO_MEMORY, "host allocation failed");
+    if (opt)
+        c->opt = *opt;
+    else
+        cc_default_options(&c->opt);
+    if (c->opt.max_slots <= 0) c->opt.max_slots = 4;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        delete c;
+        return fail(CC_ERR_CUDA, "no CUDA device available");
+    }
+    if (c->opt.device < 0 || c->opt.device >= ndev) {
+        delete c;
+        return fail(CC_ERR_INVALID_ARG, "device ordinal out of range");
+    }
+    c->device = c->opt.device;
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        delete c;
+        return fail(CC_ERR_CUDA, "cudaSetDevice failed");
+    }
+    if (c->opt.stream) {
+        c->stream = (cudaStream_t)c->opt.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(CC_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    uint64_t bytes = c->opt.hbm_budget_bytes;
+    if (c->opt.arena) {
+        if (!bytes) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(CC_ERR_INVALID_ARG, "arena given without hbm_budget_bytes");
+        }
+        c->arena_base = (char *)c->opt.arena;
+    } else {
+        if (!bytes) {
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
+            bytes = (uint64_t)(fr * 0.9);
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(CC_ERR_BUDGET, "could not allocate the HBM arena");
+        }
+        c->arena_base = (char *)p;
+        c->own_arena = true;
+    }
+    c->arena.init(c->arena_base, bytes);
+    c->timer.on = c->opt.timing != 0;
+    *out = reinterpret_cast<cc_ctx *>(c);
+    return CC_OK;
+}
+
+cc_status cc_destroy(cc_ctx *ctx)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    serve_shutdown(c);
+    {
+        std::lock_guard<std::recursive_mutex> lk(c->mu);
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+        for (auto &kv : c->graphs) graph_free(c, kv.second.get());
+        c->graphs.clear();
+        for (auto e : c->timer.pool) cudaEventDestroy(e);
+        for (auto &q : c->timer.pending) {
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
+        if (c->own_arena) cudaFree(c->arena_base);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+    return CC_OK;
+}
+
+cc_status cc_graph_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                            cc_graph_id *out)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return graph_load(c, n, row_ptr, col_idx, flags, out);
+}
+
+cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    auto it = c->graphs.find(g);
+    if (it == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    if (it->second->in_use) return fail(CC_ERR_INVALID_ARG, "graph is used by a queued or running request");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    graph_free(c, it->second.get());
+    c->graphs.erase(it);
+    return CC_OK;
+}
+
+cc_status cc_template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, int32_t root, cc_template_id *out)
+{
+    if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    TemplatePlan tp;
+    std::string err;
+    int rc = build_template_plan(k, edges, root, 1, 16.0, &tp, &err);
+    if (rc) return fail(rc, err);
+    auto t = std::make_unique<Template>();
+    t->k = k;
+    t->root_req = root;
+    if (k > 1) t->edges.assign(edges, edges + 2 * (k - 1));
+    t->aut = tp.aut;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int64_t id = c->next_id++;
+    c->templates[id] = std::move(t);
+    *out = id;
+    return CC_OK;
+}
+
+cc_status cc_template_free(cc_ctx *ctx, cc_template_id t)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if (!c->templates.erase(t)) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    return CC_OK;
+}
+
+cc_status cc_count(cc_ctx *ctx, cc_graph_id g, cc_template_id t, uint64_t seed, int32_t n_iter, uint64_t *counts,
+                   int32_t limbs_capacity, cc_result *res)
+{
+    cc_count_args a;
+    std::memset(&a, 0, sizeof a);
+    a.seed = seed;
+    a.n_iter = n_iter;
+    a.mom_groups = 1;
+    a.width_bits = -1;
+    return cc_count_ex(ctx, g, t, &a, counts, limbs_capacity, res);
+}
+
+cc_status cc_count_ex(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_count_args *args, uint64_t *counts,
+                      int32_t limbs_capacity, cc_result *res)
+{
+    if (!ctx || !args) return fail(CC_ERR_INVALID_ARG, "ctx or args is NULL");
+    if (args->n_iter < 0 || limbs_capacity < 1) return fail(CC_ERR_INVALID_ARG, "n_iter < 0 or limbs_capacity < 1");
+    if (args->n_sample < 0 || (args->n_sample > 0 && !args->sample_vertices))
+        return fail(CC_ERR_INVALID_ARG, "bad sample vertex list");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    CountJob job;
+    job.seed = args->seed;
+    job.first_iter = args->first_iter;
+    job.n_iter = args->n_iter;
+    job.mom_groups = args->mom_groups > 0 ? args->mom_groups : 1;
+    job.width_bits = args->width_bits;
+    if (args->n_sample > 0) job.sample_vertices.assign(args->sample_vertices, args->sample_vertices + args->n_sample);
+    if (res) std::memset(res, 0, sizeof *res);
+    return count_sync(c, g, t, job, counts, limbs_capacity, args->maps,
+                      args->n_sample > 0 ? args->sample_maps : nullptr, res);
+}
+
+cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out)
+{
+    if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    auto git = c->graphs.find(g);
+    auto tit = c->templates.find(t);
+    if (git == c->graphs.end() || tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown handle");
+    std::memset(out, 0, sizeof *out);
+    out->k = tit->second->k;
+    out->n_vertices = git->second->n;
+    out->n_active = git->second->n_act;
+    out->n_directed_edges = git->second->nnz;
+    if (tit->second->k == 1 || git->second->n_act == 0) return CC_OK;
+    std::unique_ptr<PlanInstance> p;
+    int n_iter = c->opt.batch > 0 ? c->opt.batch : 16;
+    CC_TRY(make_plan(c, g, t, n_iter, c->opt.width_bits, c->stream, &p));
+    out->root = p->tp.root;
+    out->n_chains = (int)p->tp.chains.size();
+    out->n_tables = out->n_chains - 1;
+    out->limbs_root = p->L_root;
+    out->batch = p->B;
+    out->n_blocks = (int64_t)p->blocks.size();
+    out->updates_per_colouring = p->updates;
+    out->gather_bytes_per_colouring = p->gather_bytes;
+    out->algorithmic_bytes_per_colouring = p->alg_bytes;
+    out->pairs_per_colouring = p->pairs;
+    out->workspace_bytes = p->ws_bytes;
+    out->table4_memory = p->tp.table4_memory;
+    out->table4_computation = p->tp.table4_computation;
+    free_plan(c, p.get());
+    return CC_OK;
+}
+
+cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out)
+{
+    if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    static const char *names[CC_KERNEL_KINDS] = {"colour", "hist", "gather", "combine", "reduce", "fused", "other", "-"};
+    std::memset(out, 0, sizeof *out);
+    for (int i = 0; i < CC_KERNEL_KINDS; i++) {
+        out->name[i] = names[i];
+        out->launches[i] = c->timer.launches[i];
+        out->seconds[i] = c->timer.seconds[i];
+        out->bytes[i] = c->timer.bytes[i];
+    }
+    out->total_launches = c->launches.load();
+    return CC_OK;
+}
+
+cc_status cc_kernel_stats_reset(cc_ctx *ctx)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    for (int i = 0; i < CC_KERNEL_KINDS; i++) {
+        c->timer.launches[i] = 0;
+        c->timer.seconds[i] = 0;
+        c->timer.bytes[i] = 0;
+    }
+    c->launches = 0;
+    return CC_OK;
+}
+
+cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_t order, int64_t *memory,
+                           int64_t *computation)
+{
+    if (!memory || !computation) return fail(CC_ERR_INVALID_ARG, "NULL output");
+    if (root < 0) return fail(CC_ERR_INVALID_ARG, "root must be given");
+    TemplatePlan tp;
+    std::string err;
+    int rc = build_template_plan(k, edges, root, order == 1 ? 1 : 0, 16.0, &tp, &err);
+    if (rc) return fail(rc, err);
+    *memory = tp.table4_memory;
+    *computation = tp.table4_computation;
+    return CC_OK;
+}
+
+cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *aut)
+{
+    if (!aut) return fail(CC_ERR_INVALID_ARG, "aut is NULL");
+    TemplatePlan tp;
+    std::string err;
+    int rc = build_template_plan(k, edges, 0, 0, 16.0, &tp, &err);
+    if (rc) return fail(rc, err);
+    *aut = tp.aut;
+    return CC_OK;
+}
+
+cc_status cc_submit(cc_ctx *ctx, const cc_request *req, cc_req_id *out)
+{
+    if (!ctx || !req || !out) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    return serve_submit(reinterpret_cast<Ctx *>(ctx), req, out);
+}
+
+cc_status cc_poll(cc_ctx *ctx, cc_req_id id, cc_result *res, uint64_t *counts, int32_t limbs_capacity)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    return serve_poll(reinterpret_cast<Ctx *>(ctx), id, res, counts, limbs_capacity, false, 0);
+}
+
+cc_status cc_wait(cc_ctx *ctx, cc_req_id id, int64_t timeout_ns, cc_result *res, uint64_t *counts,
+                  int32_t limbs_capacity)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    return serve_poll(reinterpret_cast<Ctx *>(ctx), id, res, counts, limbs_capacity, true, timeout_ns);
+}
+
+cc_status cc_cancel(cc_ctx *ctx, cc_req_id id)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    return serve_cancel(reinterpret_cast<Ctx *>(ctx), id);
+}
+
+cc_status cc_serve_stats_get(cc_ctx *ctx, cc_serve_stats *out)
+{
+    if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    return serve_stats(reinterpret_cast<Ctx *>(ctx), out);
+}
+
+}  // extern "C"

@@ -1,0 +1,727 @@
+// exec.cpp -- planning a template against a graph (integer widths, batch size,
+// vertex blocks, static workspace layout) and running the per-colouring DP
+// schedule (Algorithm 1's inner loop) as a sequence of kernel launches.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "runtime.h"
+
+namespace cc {
+
+uint64_t splitmix64_host(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+namespace {
+
+constexpr uint64_t kAl = 256;
+inline uint64_t rup(uint64_t x) { return (x + kAl - 1) / kAl * kAl; }
+
+int bits_for(double v)
+{
+    if (!(v >= 1.0)) return 1;
+    // v is an upper bound computed in FP64; widen by a relative 1e-9 before taking bits
+    return (int)std::floor(std::log2(v * (1.0 + 1e-9))) + 1;
+}
+
+// Rooted homomorphism counts (no colours): H_x(v) = prod over children c of
+// sum_{u in N(v)} H_c(u), H_leaf = 1.  Every table entry X_x[v][S] counts a
+// subset of these maps, so max_v H_x bounds the table and sum_v H_root bounds
+// the total.
+cc_status hom_bounds(Ctx *c, Graph *g, const TemplatePlan &tp, cudaStream_t st, std::vector<double> *log2max,
+                     double *log2sum_root)
+{
+    const int nc = (int)tp.chains.size();
+    log2max->assign(nc, 0.0);
+    bool all = true;
+    for (int i = 0; i < nc; i++) {
+        auto it = g->hom_cache.find(tp.chains[i].canon);
+        if (it == g->hom_cache.end()) all = false;
+    }
+    if (!all) {
+        std::vector<double *> H(nc, nullptr);
+        double *red = (double *)c->arena.alloc(16);
+        bool ok = red != nullptr;
+        for (int i = 0; i < nc && ok; i++) {
+            H[i] = (double *)c->arena.alloc(sizeof(double) * std::max<int64_t>(g->n_act, 1));
+            ok = H[i] != nullptr;
+        }
+        if (!ok) {
+            for (auto p : H) c->arena.free(p);
+            c->arena.free(red);
+            return fail(CC_ERR_BUDGET, "no room for the homomorphism bound vectors");
+        }
+        for (int i = 0; i < nc; i++) {
+            launch_fill_double(st, g->n_act, 1.0, H[i]);
+            for (auto &s : tp.chains[i].steps)
+                launch_hom_step(st, g->n_act, g->row_ptr, g->col_idx, s.src_chain < 0 ? nullptr : H[s.src_chain],
+                                H[i]);
+            double ms[2] = {0, 0};
+            CC_CUDA(cudaMemsetAsync(red, 0, 16, st));
+            launch_max_sum(st, g->n_act, H[i], red);
+            CC_CUDA(cudaMemcpyAsync(ms, red, 16, cudaMemcpyDeviceToHost, st));
+            CC_CUDA(cudaStreamSynchronize(st));
+            c->launches += 3 + (int64_t)tp.chains[i].steps.size();
+            g->hom_cache[tp.chains[i].canon] = {ms[0] > 0 ? std::log2(ms[0]) : -1.0,
+                                                ms[1] > 0 ? std::log2(ms[1]) : -1.0};
+        }
+        CC_CUDA(cudaGetLastError());
+        for (auto p : H) c->arena.free(p);
+        c->arena.free(red);
+    }
+    for (int i = 0; i < nc; i++) (*log2max)[i] = g->hom_cache[tp.chains[i].canon].first;
+    *log2sum_root = g->hom_cache[tp.chains[nc - 1].canon].second;
+    return CC_OK;
+}
+
+int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(l2, 1000.0))); }
+
+struct Layout {
+    uint64_t bytes = 0;
+    uint64_t off_col, off_hist, off_act[2], off_agg, off_partial, off_root, off_scratch, off_totals, off_params;
+    std::vector<uint64_t> off_table;
+    int64_t max_tasks = 0;
+    std::vector<std::pair<int64_t, int64_t>> blocks;
+    std::vector<PlanInstance::BlockHeavy> heavy;
+};
+
+// Static workspace layout for batch B and block size V.  Count tables are
+// placed first-fit over their lifetimes (a table lives from its chain to its
+// last consumer), so memory is reused as soon as the schedule is done with it.
+Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp, int B, int64_t V)
+{
+    const TemplatePlan &tp = p.tp;
+    const int k = tp.k;
+    Layout Lo;
+    const int64_t n = g.n_act;
+    // blocks and their heavy ranges
+    for (int64_t v0 = 0; v0 < n; v0 += V) Lo.blocks.push_back({v0, std::min(n, v0 + V)});
+    for (auto &b : Lo.blocks) {
+        PlanInstance::BlockHeavy h;
+        h.h0 = std::lower_bound(sp.h_heavy_v.begin(), sp.h_heavy_v.end(), (int32_t)b.first) - sp.h_heavy_v.begin();
+        h.h1 = std::lower_bound(sp.h_heavy_v.begin(), sp.h_heavy_v.end(), (int32_t)b.second) - sp.h_heavy_v.begin();
+        h.t0 = sp.h_heavy_tptr[h.h0];
+        h.t1 = sp.h_heavy_tptr[h.h1];
+        Lo.max_tasks = std::max(Lo.max_tasks, h.t1 - h.t0);
+        Lo.heavy.push_back(h);
+    }
+    // per-chain table sizes and lifetimes
+    const int nc = (int)tp.chains.size();
+    Lo.off_table.assign(nc, ~0ull);
+    struct Placed { uint64_t off, size; int start, end; };
+    std::vector<Placed> placed;
+    uint64_t top = 0;
+    for (int i = 0; i < nc; i++) {
+        const auto &C = tp.chains[i];
+        if (C.is_root) continue;
+        uint64_t sz = rup((uint64_t)n * B * binom(k, C.size) * 8 * p.chain_L[i]);
+        int start = i, end = C.last_consumer;
+        // lowest offset not overlapping any live placed table
+        std::vector<std::pair<uint64_t, uint64_t>> busy;
+        for (auto &q : placed)
+            if (!(q.end < start || q.start > end)) busy.push_back({q.off, q.off + q.size});
+        std::sort(busy.begin(), busy.end());
+        uint64_t off = 0;
+        for (auto &b : busy) {
+            if (off + sz <= b.first) break;
+            off = std::max(off, b.second);
+        }
+        placed.push_back({off, sz, start, end});
+        Lo.off_table[i] = off;
+        top = std::max(top, off + sz);
+    }
+    uint64_t cur = top;
+    auto take = [&](uint64_t bytes) {
+        uint64_t o = cur;
+        cur += rup(bytes);
+        return o;
+    };
+    // widest intermediate and aggregate rows
+    int64_t maxAct = 1, maxP = 1;
+    bool need_hist = false;
+    for (auto &C : tp.chains)
+        for (size_t si = 0; si < C.steps.size(); si++) {
+            const auto &s = C.steps[si];
+            if (si + 1 < C.steps.size()) maxAct = std::max<int64_t>(maxAct, binom(k, s.h));
+            if (s.src_chain >= 0) maxP = std::max<int64_t>(maxP, binom(k, s.p));
+            else need_hist = true;
+        }
+    const int Lm = p.Lmax;
+    Lo.off_col = take((uint64_t)n * B);
+    Lo.off_hist = need_hist ? take((uint64_t)n * B * k * 4) : 0;
+    Lo.off_act[0] = take((uint64_t)V * B * maxAct * 8 * Lm);
+    Lo.off_act[1] = take((uint64_t)V * B * maxAct * 8 * Lm);
+    Lo.off_agg = take((uint64_t)V * B * maxP * 8 * Lm);
+    Lo.off_partial = take((uint64_t)std::max<int64_t>(Lo.max_tasks, 1) * B * maxP * 8 * Lm);
+    Lo.off_root = take((uint64_t)V * B * 8 * p.L_root);
+    Lo.off_scratch = take((uint64_t)reduce_scratch_ctas() * B * 8 * p.L_root);
+    Lo.off_totals = take((uint64_t)B * 8 * p.L_root);
+    Lo.off_params = take(sizeof(ColourParams));
+    Lo.bytes = cur;
+    return Lo;
+}
+
+}  // namespace
+
+cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
+                    std::unique_ptr<PlanInstance> *out)
+{
+    auto git = c->graphs.find(gid);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    auto tit = c->templates.find(tid);
+    if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    Graph *g = git->second.get();
+    Template *t = tit->second.get();
+    auto p = std::make_unique<PlanInstance>();
+    p->graph_id = gid;
+    p->tmpl_id = tid;
+    std::string err;
+    double avg = g->n_act ? (double)g->nnz / g->n_act : 1.0;
+    int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &p->tp, &err);
+    if (rc) return fail(rc, err);
+    const TemplatePlan &tp = p->tp;
+    const int k = tp.k;
+    const int nc = (int)tp.chains.size();
+    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
+        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
+    p->width_bits = width_bits;
+    p->exact = width_bits == 0;
+    p->chain_L.assign(nc, 1);
+    if (k >= 2 && g->n_act > 0) {
+        if (width_bits == 0) {
+            std::vector<double> l2max;
+            double l2sum;
+            CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum));
+            int rb = bits_from_log2(l2sum);
+            if (rb > 256)
+                return fail(CC_ERR_WIDTH, "exact counts may need " + std::to_string(rb) +
+                                              " bits (> 256); request a fixed width_bits for residues");
+            p->L_root = (rb + 63) / 64;
+            for (int i = 0; i < nc; i++) {
+                int b = bits_from_log2(l2max[i]);
+                p->chain_L[i] = tp.chains[i].is_root ? p->L_root : std::min(p->L_root, (b + 63) / 64);
+            }
+        } else {
+            p->L_root = width_bits / 64;
+            for (auto &L : p->chain_L) L = p->L_root;
+        }
+    } else {
+        p->L_root = 1;
+    }
+    p->Lmax = *std::max_element(p->chain_L.begin(), p->chain_L.end());
+    // split threshold and batch / block size under the budget
+    p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : 1024;
+    CC_TRY(ensure_split(c, g, p->split, st));
+    const Graph::Split &sp = g->splits[p->split];
+    int Bmax = c->opt.batch > 0 ? c->opt.batch : 16;
+    Bmax = std::max(1, std::min({Bmax, n_iter > 0 ? n_iter : 1, 64}));
+    const uint64_t room = c->arena.largest_free();
+    const int64_t n = std::max<int64_t>(g->n_act, 1);
+    bool found = false;
+    Layout Lo;
+    for (int B = Bmax; B >= 1 && !found; B--) {
+        int64_t V = c->opt.block_vertices > 0 ? std::min<int64_t>(c->opt.block_vertices, n) : n;
+        while (true) {
+            Lo = layout_for(*p, *g, sp, B, V);
+            if (Lo.bytes + (64ull << 20) <= room) {
+                found = true;
+                p->B = B;
+                p->V = V;
+                break;
+            }
+            if (V <= 4096 || c->opt.block_vertices > 0) break;
+            V = (V + 1) / 2;
+        }
+        if (c->opt.batch > 0 && !found) break;
+    }
+    if (!found) return fail(CC_ERR_BUDGET, "plan does not fit the HBM budget (largest free block " +
+                                               std::to_string(room >> 20) + " MiB)");
+    p->ws_bytes = Lo.bytes;
+    p->off_col = Lo.off_col;
+    p->off_hist = Lo.off_hist;
+    p->off_act[0] = Lo.off_act[0];
+    p->off_act[1] = Lo.off_act[1];
+    p->off_agg = Lo.off_agg;
+    p->off_partial = Lo.off_partial;
+    p->off_root = Lo.off_root;
+    p->off_scratch = Lo.off_scratch;
+    p->off_totals = Lo.off_totals;
+    p->off_params = Lo.off_params;
+    p->off_table = Lo.off_table;
+    p->blocks = Lo.blocks;
+    p->heavy = Lo.heavy;
+    p->max_tasks = Lo.max_tasks;
+    // device constants: rm tables (h = 1..k) and pair tables for generic steps
+    SetTables T;
+    T.build(k);
+    std::vector<std::pair<int, int>> need_pairs;
+    for (auto &C : tp.chains)
+        for (auto &s : C.steps)
+            if (s.a >= 2 && s.src_chain >= 0) need_pairs.push_back({s.h, s.a});
+    std::sort(need_pairs.begin(), need_pairs.end());
+    need_pairs.erase(std::unique(need_pairs.begin(), need_pairs.end()), need_pairs.end());
+    uint64_t cbytes = 0;
+    for (int h = 1; h <= k; h++) cbytes += rup(T.rm[h].size() * 2);
+    std::vector<std::vector<uint32_t>> pt;
+    for (auto &hp : need_pairs) {
+        pt.push_back(T.pairs(hp.first, hp.second));
+        cbytes += rup(pt.back().size() * 4);
+    }
+    p->consts = c->arena.alloc(std::max<uint64_t>(cbytes, 256));
+    if (!p->consts) return fail(CC_ERR_BUDGET, "no room for colour-set tables");
+    char *cp = (char *)p->consts;
+    p->d_rm.assign(k + 1, nullptr);
+    for (int h = 1; h <= k; h++) {
+        p->d_rm[h] = (uint16_t *)cp;
+        CC_CUDA(cudaMemcpyAsync(cp, T.rm[h].data(), T.rm[h].size() * 2, cudaMemcpyHostToDevice, st));
+        cp += rup(T.rm[h].size() * 2);
+    }
+    for (size_t i = 0; i < need_pairs.size(); i++) {
+        p->d_pairs[need_pairs[i]] = (uint32_t *)cp;
+        CC_CUDA(cudaMemcpyAsync(cp, pt[i].data(), pt[i].size() * 4, cudaMemcpyHostToDevice, st));
+        cp += rup(pt[i].size() * 4);
+    }
+    CC_CUDA(cudaStreamSynchronize(st));
+    // analytic per-colouring figures
+    const double nnz = (double)g->nnz, na = (double)g->n_act;
+    int gather_passes = 0;
+    for (int i = 0; i < nc; i++) {
+        const auto &C = tp.chains[i];
+        for (auto &s : C.steps) {
+            double pairs_v = s.a == 1 ? (double)binom(k, s.h)
+                                      : (s.p == 1 ? (double)binom(k, s.h) * s.h : (double)binom(k, s.h) * binom(s.h, s.a));
+            p->pairs += na * pairs_v;
+            if (s.src_chain >= 0 && !s.reuse_agg) {
+                double cols = (double)binom(k, s.p);
+                p->updates += nnz * cols;
+                p->gather_bytes += nnz * cols * 8.0 * p->chain_L[s.src_chain];
+                gather_passes++;
+            }
+        }
+        if (!C.is_root) p->alg_bytes += na * (double)binom(k, C.size) * 8.0 * p->chain_L[i];
+    }
+    p->alg_bytes += p->gather_bytes;
+    p->alg_bytes += gather_passes * (4.0 * nnz + 8.0 * (na + 1)) / p->B;  // CSR, shared by the pass
+    bool any_leaf = false;
+    for (auto &C : tp.chains)
+        for (auto &s : C.steps) any_leaf |= s.src_chain < 0;
+    if (any_leaf) p->alg_bytes += nnz + (4.0 * nnz + 8.0 * (na + 1)) / p->B;  // colour bytes + CSR
+    *out = std::move(p);
+    return CC_OK;
+}
+
+void free_plan(Ctx *c, PlanInstance *p)
+{
+    if (!p) return;
+    c->arena.free(p->consts);
+    p->consts = nullptr;
+}
+
+namespace {
+
+struct Launcher {
+    Ctx *c;
+    cudaStream_t st;
+    KernelTimer &T;
+    Launcher(Ctx *c_, cudaStream_t s) : c(c_), st(s), T(c_->timer) {}
+    int kind = -1;
+    cudaEvent_t ea = nullptr;
+    cudaEvent_t get_event()
+    {
+        if (T.pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = T.pool.back();
+        T.pool.pop_back();
+        return e;
+    }
+    void begin(int k_)
+    {
+        kind = k_;
+        if (T.on) {
+            ea = get_event();
+            cudaEventRecord(ea, st);
+        }
+    }
+    void end(int nlaunch, double bytes)
+    {
+        c->launches += nlaunch;
+        T.launches[kind] += nlaunch;
+        T.total_launches += nlaunch;
+        T.bytes[kind] += bytes;
+        if (T.on) {
+            cudaEvent_t eb = get_event();
+            cudaEventRecord(eb, st);
+            T.pending.push_back({ea, eb, kind, bytes});
+        }
+    }
+};
+
+}  // namespace
+
+// Resolve pending event pairs into the per-kind totals (after a stream sync).
+static void drain_timer(Ctx *c)
+{
+    auto &T = c->timer;
+    for (auto &q : T.pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) T.seconds[q.kind] += ms * 1e-3;
+        T.pool.push_back(q.a);
+        T.pool.push_back(q.b);
+    }
+    cudaGetLastError();
+    T.pending.clear();
+}
+
+static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st, const int64_t *d_samples,
+                             int64_t n_samples, uint64_t *d_samples_out)
+{
+    Graph *g = c->graphs.at(p->graph_id).get();
+    const TemplatePlan &tp = p->tp;
+    const int k = tp.k, B = p->B;
+    const Graph::Split &sp = g->splits.at(p->split);
+    Launcher Ln(c, st);
+    auto W = [&](uint64_t off) { return ws + off; };
+    uint64_t *totals = (uint64_t *)W(p->off_totals);
+    CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)B * 8 * p->L_root, st));
+    uint8_t *col = (uint8_t *)W(p->off_col);
+    Ln.begin(K_COLOUR);
+    launch_colour(st, g->n_act, B, k, g->orig, (const ColourParams *)W(p->off_params), col);
+    Ln.end(1, (double)g->n_act * (8 + B));
+    uint32_t *hist = (uint32_t *)W(p->off_hist);
+    bool need_hist = false;
+    for (auto &C : tp.chains)
+        for (auto &s : C.steps) need_hist |= s.src_chain < 0;
+    if (need_hist) {
+        Ln.begin(K_HIST);
+        launch_hist(st, 0, g->n_act, B, k, g->row_ptr, g->col_idx, col, hist);
+        Ln.end(1, (double)g->nnz * (4 + B) + (double)g->n_act * (8 + 4.0 * B * k));
+    }
+    for (size_t ci = 0; ci < tp.chains.size(); ci++) {
+        const ChainPlan &C = tp.chains[ci];
+        const int L = p->chain_L[ci];
+        for (size_t bi = 0; bi < p->blocks.size(); bi++) {
+            const int64_t v0 = p->blocks[bi].first, v1 = p->blocks[bi].second, nv = v1 - v0;
+            const auto &hv = p->heavy[bi];
+            const uint64_t *cur = nullptr;
+            int64_t cur_cols = k;
+            uint64_t *root_rows = (uint64_t *)W(p->off_root);
+            for (size_t si = 0; si < C.steps.size(); si++) {
+                const Step &s = C.steps[si];
+                const bool last = si + 1 == C.steps.size();
+                const int64_t Ch = binom(k, s.h);
+                uint64_t *out;
+                if (last)
+                    out = C.is_root ? root_rows
+                                    : (uint64_t *)W(p->off_table[ci]) + (uint64_t)v0 * B * Ch * L;
+                else
+                    out = (uint64_t *)W(p->off_act[si & 1]);
+                if (s.src_chain < 0) {
+                    const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
+                    Ln.begin(K_COMBINE);
+                    if (s.a == 1)
+                        launch_combine_select(st, L, true, v0, nv, B, k, Ch, k, p->d_rm[s.h], col, hrow, out);
+                    else
+                        launch_combine_hist(st, L, v0, nv, B, k, Ch, cur_cols, s.h, p->d_rm[s.h], cur, hrow, out);
+                    Ln.end(1, (double)nv * B * Ch * 8 * L);
+                } else {
+                    const int Ls = p->chain_L[s.src_chain];
+                    const int64_t Cp = binom(k, s.p);
+                    const int64_t R = (int64_t)B * Cp;
+                    const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                    uint64_t *agg = (uint64_t *)W(p->off_agg);
+                    if (!s.reuse_agg) {
+                        // algorithmic bytes of this gather: neighbour rows + CSR + aggregate write
+                        double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                        double bytes = e_blk * R * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * R * 8.0 * L;
+                        Ln.begin(K_GATHER);
+                        launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
+                        int nl = 1;
+                        if (hv.t1 > hv.t0) {
+                            uint64_t *part = (uint64_t *)W(p->off_partial);
+                            launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
+                            launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R,
+                                                 agg);
+                            nl += 2;
+                        }
+                        Ln.end(nl, bytes);
+                    }
+                    Ln.begin(K_COMBINE);
+                    if (s.a == 1)
+                        launch_combine_select(st, L, false, v0, nv, B, k, Ch, Cp, p->d_rm[s.h], col, agg, out);
+                    else
+                        launch_combine_generic(st, L, nv, B, Ch, cur_cols, Cp, binom(s.h, s.a), p->d_pairs.at({s.h, s.a}),
+                                               cur, agg, out);
+                    Ln.end(1, (double)nv * B * Ch * 8 * L);
+                }
+                cur = out;
+                cur_cols = Ch;
+            }
+            if (C.is_root) {
+                Ln.begin(K_REDUCE);
+                launch_root_reduce(st, p->L_root, nv, B, root_rows, (uint64_t *)W(p->off_scratch),
+                                   reduce_scratch_ctas(), totals);
+                int nl = 2;
+                if (n_samples > 0) {
+                    launch_sample_extract(st, p->L_root, n_samples, d_samples, v0, v1, B, root_rows, d_samples_out);
+                    nl++;
+                }
+                Ln.end(nl, (double)nv * B * 8 * p->L_root);
+            }
+        }
+    }
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+}
+
+cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int pass0, int pass1,
+                     cudaStream_t st, ColourParams *host_params, uint64_t *host_totals, uint64_t *host_samples,
+                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out)
+{
+    const int B = p->B;
+    for (int ps = pass0; ps < pass1; ps++) {
+        ColourParams &hp = host_params[ps];
+        const uint64_t fs = splitmix64_host(job.seed);
+        for (int b = 0; b < B; b++)
+            hp.hj[b] = splitmix64_host(fs + (uint64_t)(job.first_iter + (int64_t)ps * B + b));
+        CC_CUDA(cudaMemcpyAsync(ws + p->off_params, &hp, sizeof(ColourParams), cudaMemcpyHostToDevice, st));
+        CC_TRY(launch_pass(c, p, ws, st, d_samples, n_samples, d_samples_out));
+        CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * B * p->L_root, ws + p->off_totals,
+                                (size_t)B * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
+        if (n_samples > 0)
+            CC_CUDA(cudaMemcpyAsync(host_samples + (size_t)ps * B * n_samples * p->L_root, d_samples_out,
+                                    (size_t)B * n_samples * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
+        if (c->timer.on) {
+            CC_CUDA(cudaStreamSynchronize(st));
+            drain_timer(c);
+        }
+    }
+    return CC_OK;
+}
+
+namespace {
+
+// q = x / d, returns remainder (x has L limbs)
+uint64_t divmod_small(const uint64_t *x, int L, uint64_t d, uint64_t *q)
+{
+    unsigned __int128 r = 0;
+    for (int i = L - 1; i >= 0; i--) {
+        unsigned __int128 cur = (r << 64) | x[i];
+        q[i] = (uint64_t)(cur / d);
+        r = cur % d;
+    }
+    return (uint64_t)r;
+}
+
+double to_double(const uint64_t *x, int L)
+{
+    double d = 0;
+    for (int i = L - 1; i >= 0; i--) d = d * 18446744073709551616.0 + (double)x[i];
+    return d;
+}
+
+}  // namespace
+
+cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
+                        const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
+                        uint64_t *sample_out, cc_result *res)
+{
+    (void)c;
+    const int k = p->tp.k, L = p->L_root, B = p->B;
+    const int n_iter = job.n_iter;
+    const int64_t ns = (int64_t)job.sample_vertices.size();
+    cc_result r;
+    std::memset(&r, 0, sizeof r);
+    r.k = k;
+    r.limbs = L;
+    r.exact = p->exact ? 1 : 0;
+    r.n_iter = n_iter;
+    r.aut = p->tp.aut;
+    r.root = p->tp.root;
+    r.batch = B;
+    r.workspace_bytes = p->ws_bytes;
+    if (cap < L) {
+        if (res) *res = r;
+        return fail(CC_ERR_CAPACITY, "limbs_capacity " + std::to_string(cap) + " < needed " + std::to_string(L));
+    }
+    std::vector<double> est(n_iter);
+    double kk = std::pow((double)k, (double)k), kf = 1;
+    for (int i = 2; i <= k; i++) kf *= i;
+    std::vector<uint64_t> q(L);
+    for (int j = 0; j < n_iter; j++) {
+        const int ps = j / B, b = j % B;
+        const uint64_t *m = totals + ((size_t)ps * B + b) * L;
+        if (maps)
+            for (int l = 0; l < cap; l++) maps[(size_t)j * cap + l] = l < L ? m[l] : 0;
+        if (p->exact) {
+            uint64_t rem = divmod_small(m, L, (uint64_t)p->tp.aut, q.data());
+            if (rem) return fail(CC_ERR_INTERNAL, "labelled map count not divisible by |Aut(T)|");
+            for (int l = 0; l < cap; l++) counts[(size_t)j * cap + l] = l < L ? q[l] : 0;
+            est[j] = to_double(q.data(), L) * (kk / kf);
+        } else {
+            for (int l = 0; l < cap; l++) counts[(size_t)j * cap + l] = l < L ? m[l] : 0;
+        }
+        if (sample_out && ns > 0) {
+            for (int64_t s = 0; s < ns; s++) {
+                uint64_t *dst = sample_out + ((size_t)j * ns + s) * cap;
+                int64_t ov = job.sample_vertices[s];
+                int64_t cv = (ov >= 0 && ov < g->n) ? g->h_new_id[ov] : -1;
+                for (int l = 0; l < cap; l++) dst[l] = 0;
+                if (cv >= 0 && samples) {
+                    const uint64_t *src = samples + (((size_t)ps * B + b) * ns + s) * L;
+                    for (int l = 0; l < L; l++) dst[l] = src[l];
+                }
+            }
+        }
+    }
+    if (p->exact && n_iter > 0) {
+        double s = 0;
+        for (double e : est) s += e;
+        r.estimate = s / n_iter;
+        int t = std::max(1, std::min(job.mom_groups, n_iter));
+        int qsz = n_iter / t;
+        std::vector<double> means;
+        for (int gi = 0; gi < t; gi++) {
+            double a = 0;
+            for (int i = gi * qsz; i < (gi + 1) * qsz; i++) a += est[i];
+            means.push_back(a / qsz);
+        }
+        std::sort(means.begin(), means.end());
+        r.median_of_means = (t % 2) ? means[t / 2] : 0.5 * (means[t / 2 - 1] + means[t / 2]);
+    }
+    if (res) {
+        double dev = res->device_seconds, wall = res->wall_seconds;
+        int64_t kl = res->kernel_launches;
+        *res = r;
+        res->device_seconds = dev;
+        res->wall_seconds = wall;
+        res->kernel_launches = kl;
+    }
+    return CC_OK;
+}
+
+// special cases with no DP: k = 1 (every vertex, isolated ones included), or no edges
+static cc_status trivial_counts(Graph *g, const CountJob &job, int k, int64_t aut, uint64_t *counts, int32_t cap,
+                                uint64_t *maps, uint64_t *sample_out, cc_result *res)
+{
+    if (cap < 1) return fail(CC_ERR_CAPACITY, "limbs_capacity < 1");
+    const uint64_t v = (k == 1) ? (uint64_t)g->n : 0;
+    double kk = std::pow((double)k, (double)k), kf = 1;
+    for (int i = 2; i <= k; i++) kf *= i;
+    for (int j = 0; j < job.n_iter; j++) {
+        for (int l = 0; l < cap; l++) {
+            counts[(size_t)j * cap + l] = l == 0 ? v : 0;
+            if (maps) maps[(size_t)j * cap + l] = l == 0 ? v : 0;
+        }
+        for (size_t s = 0; sample_out && s < job.sample_vertices.size(); s++)
+            for (int l = 0; l < cap; l++) {
+                int64_t ov = job.sample_vertices[s];
+                sample_out[((size_t)j * job.sample_vertices.size() + s) * cap + l] =
+                    (l == 0 && k == 1 && ov >= 0 && ov < g->n) ? 1 : 0;
+            }
+    }
+    if (res) {
+        std::memset(res, 0, sizeof *res);
+        res->k = k;
+        res->limbs = 1;
+        res->exact = 1;
+        res->n_iter = job.n_iter;
+        res->aut = aut;
+        res->estimate = (double)v * kk / kf;
+        res->median_of_means = res->estimate;
+        res->batch = 1;
+    }
+    return CC_OK;
+}
+
+cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
+                     uint64_t *maps, uint64_t *sample_out, cc_result *res)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    if (!counts) return fail(CC_ERR_INVALID_ARG, "counts is NULL");
+    if (job.n_iter < 0) return fail(CC_ERR_INVALID_ARG, "n_iter < 0");
+    auto git = c->graphs.find(gid);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    auto tit = c->templates.find(tid);
+    if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    Graph *g = git->second.get();
+    Template *t = tit->second.get();
+    const int width = job.width_bits >= 0 ? job.width_bits : c->opt.width_bits;
+    if (t->k == 1 || g->n_act == 0 || job.n_iter == 0)
+        return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res);
+    cudaStream_t st = c->stream;
+    std::unique_ptr<PlanInstance> p;
+    CC_TRY(make_plan(c, gid, tid, job.n_iter, width, st, &p));
+    struct Cleanup {
+        Ctx *c;
+        PlanInstance *p;
+        char *ws = nullptr;
+        int64_t *ds = nullptr;
+        uint64_t *dso = nullptr;
+        void *hp = nullptr, *ht = nullptr, *hs = nullptr;
+        ~Cleanup()
+        {
+            cudaStreamSynchronize(c->stream);
+            c->arena.free(ws);
+            c->arena.free(ds);
+            c->arena.free(dso);
+            if (hp) cudaFreeHost(hp);
+            if (ht) cudaFreeHost(ht);
+            if (hs) cudaFreeHost(hs);
+            free_plan(c, p);
+        }
+    } cl{c, p.get()};
+    cl.ws = (char *)c->arena.alloc(p->ws_bytes);
+    if (!cl.ws) return fail(CC_ERR_BUDGET, "workspace does not fit the HBM budget");
+    const int B = p->B;
+    const int npass = (job.n_iter + B - 1) / B;
+    const int64_t ns = (int64_t)job.sample_vertices.size();
+    if (ns > 0) {
+        std::vector<int64_t> cv(ns);
+        for (int64_t s = 0; s < ns; s++) {
+            int64_t ov = job.sample_vertices[s];
+            cv[s] = (ov >= 0 && ov < g->n) ? g->h_new_id[ov] : -1;
+        }
+        cl.ds = (int64_t *)c->arena.alloc(8 * ns);
+        cl.dso = (uint64_t *)c->arena.alloc((uint64_t)8 * ns * B * p->L_root);
+        if (!cl.ds || !cl.dso) return fail(CC_ERR_BUDGET, "no room for sampled vertices");
+        CC_CUDA(cudaMemcpyAsync(cl.ds, cv.data(), 8 * ns, cudaMemcpyHostToDevice, st));
+        CC_CUDA(cudaMemsetAsync(cl.dso, 0, (size_t)8 * ns * B * p->L_root, st));
+    }
+    CC_CUDA(cudaMallocHost(&cl.hp, sizeof(ColourParams) * npass));
+    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root));
+    if (ns > 0) CC_CUDA(cudaMallocHost(&cl.hs, (size_t)8 * npass * B * ns * p->L_root));
+    cudaEvent_t e0, e1;
+    CC_CUDA(cudaEventCreate(&e0));
+    CC_CUDA(cudaEventCreate(&e1));
+    int64_t l0 = c->launches.load();
+    CC_CUDA(cudaEventRecord(e0, st));
+    cc_status rc = run_passes(c, p.get(), cl.ws, job, 0, npass, st, (ColourParams *)cl.hp, (uint64_t *)cl.ht,
+                              (uint64_t *)cl.hs, cl.ds, ns, cl.dso);
+    CC_CUDA(cudaEventRecord(e1, st));
+    CC_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CC_OK) return rc;
+    if (res) {
+        res->device_seconds = ms * 1e-3;
+        res->kernel_launches = c->launches.load() - l0;
+    }
+    rc = finish_counts(c, p.get(), g, job, (const uint64_t *)cl.ht, (const uint64_t *)cl.hs, counts, cap, maps,
+                       sample_out, res);
+    if (res)
+        res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return rc;
+}
+
+}  // namespace cc

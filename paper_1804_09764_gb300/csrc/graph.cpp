@@ -1,0 +1,192 @@
+// graph.cpp -- loading a CSR graph onto the device, neighbour-list task
+// splitting (Algorithm 4), and rooted homomorphism bounds used to size the
+// integers of each count table.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "runtime.h"
+
+namespace cc {
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cc_status validate_host(int64_t n, const int64_t *rp, const int32_t *ci)
+{
+    std::vector<int32_t> sorted(ci, ci + rp[n]);
+    for (int64_t v = 0; v < n; v++) {
+        auto b = sorted.begin() + rp[v], e = sorted.begin() + rp[v + 1];
+        for (auto it = b; it != e; ++it) {
+            if (*it < 0 || *it >= n) return fail(CC_ERR_BAD_GRAPH, "neighbour id out of range at vertex " + std::to_string(v));
+            if (*it == v) return fail(CC_ERR_BAD_GRAPH, "self-loop at vertex " + std::to_string(v));
+        }
+        std::sort(b, e);
+        if (std::adjacent_find(b, e) != e) return fail(CC_ERR_BAD_GRAPH, "duplicate edge at vertex " + std::to_string(v));
+    }
+    for (int64_t v = 0; v < n; v++)
+        for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
+            int64_t u = sorted[e];
+            if (!std::binary_search(sorted.begin() + rp[u], sorted.begin() + rp[u + 1], (int32_t)v))
+                return fail(CC_ERR_BAD_GRAPH, "edge " + std::to_string(v) + "-" + std::to_string(u) +
+                                                  " has no reverse direction");
+        }
+    return CC_OK;
+}
+
+}  // namespace
+
+cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                     cc_graph_id *out)
+{
+    if (!out) return fail(CC_ERR_INVALID_ARG, "out is NULL");
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(CC_ERR_INVALID_ARG, "n out of range");
+    if (!row_ptr) return fail(CC_ERR_INVALID_ARG, "row_ptr is NULL");
+    cudaStream_t st = c->stream;
+    auto g = std::make_unique<Graph>();
+    g->n = n;
+    std::vector<int64_t> rp(n + 1);
+    const bool rp_dev = is_device_ptr(row_ptr);
+    if (rp_dev) {
+        CC_CUDA(cudaMemcpy(rp.data(), row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(rp.data(), row_ptr, sizeof(int64_t) * (n + 1));
+    }
+    if (rp[0] != 0) return fail(CC_ERR_BAD_GRAPH, "row_ptr[0] must be 0");
+    for (int64_t v = 0; v < n; v++)
+        if (rp[v + 1] < rp[v]) return fail(CC_ERR_BAD_GRAPH, "row_ptr decreases at " + std::to_string(v));
+    const int64_t nnz = rp[n];
+    if (nnz > 0 && !col_idx) return fail(CC_ERR_INVALID_ARG, "col_idx is NULL");
+    if (nnz >= (int64_t(1) << 40)) return fail(CC_ERR_INVALID_ARG, "too many edges");
+    const bool ci_dev = nnz > 0 && is_device_ptr(col_idx);
+    if (flags & CC_VALIDATE) {
+        std::vector<int32_t> hci;
+        const int32_t *p = col_idx;
+        if (ci_dev) {
+            hci.resize(nnz);
+            CC_CUDA(cudaMemcpy(hci.data(), col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+            p = hci.data();
+        }
+        CC_TRY(validate_host(n, rp.data(), p));
+    }
+    // compact numbering: drop isolated vertices (they are in no embedding when k >= 2)
+    g->h_new_id.assign(n, -1);
+    std::vector<int64_t> orig;
+    g->h_row_ptr.clear();
+    g->h_row_ptr.push_back(0);
+    for (int64_t v = 0; v < n; v++) {
+        int64_t d = rp[v + 1] - rp[v];
+        if (d == 0) continue;
+        g->h_new_id[v] = (int32_t)orig.size();
+        orig.push_back(v);
+        g->h_row_ptr.push_back(rp[v + 1]);  // isolated vertices hold no edges: offsets unchanged
+        g->max_degree = std::max(g->max_degree, d);
+    }
+    g->n_act = (int64_t)orig.size();
+    g->nnz = nnz;
+
+    auto A = [&](uint64_t bytes) { return c->arena.alloc(bytes); };
+    g->row_ptr = (int64_t *)A(sizeof(int64_t) * (g->n_act + 1));
+    g->col_idx = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    g->orig = (int64_t *)A(sizeof(int64_t) * std::max<int64_t>(g->n_act, 1));
+    int32_t *d_new = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(n, 1));
+    int32_t *d_src = nullptr;
+    if (nnz > 0 && !ci_dev) d_src = (int32_t *)A(sizeof(int32_t) * nnz);
+    if (!g->row_ptr || !g->col_idx || !g->orig || !d_new || (nnz > 0 && !ci_dev && !d_src)) {
+        c->arena.free(g->row_ptr);
+        c->arena.free(g->col_idx);
+        c->arena.free(g->orig);
+        c->arena.free(d_new);
+        c->arena.free(d_src);
+        return fail(CC_ERR_BUDGET, "graph does not fit the HBM budget");
+    }
+    CC_CUDA(cudaMemcpyAsync(g->row_ptr, g->h_row_ptr.data(), sizeof(int64_t) * (g->n_act + 1),
+                            cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaMemcpyAsync(g->orig, orig.data(), sizeof(int64_t) * g->n_act, cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaMemcpyAsync(d_new, g->h_new_id.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    if (nnz > 0) {
+        const int32_t *src = col_idx;
+        if (!ci_dev) {
+            CC_CUDA(cudaMemcpyAsync(d_src, col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+            src = d_src;
+        }
+        launch_remap(st, nnz, src, d_new, g->col_idx);
+        c->launches++;
+    }
+    CC_CUDA(cudaGetLastError());
+    CC_CUDA(cudaStreamSynchronize(st));
+    c->arena.free(d_new);
+    c->arena.free(d_src);
+    int64_t id = c->next_id++;
+    c->graphs[id] = std::move(g);
+    *out = id;
+    return CC_OK;
+}
+
+cc_status graph_free(Ctx *c, Graph *g)
+{
+    c->arena.free(g->row_ptr);
+    c->arena.free(g->col_idx);
+    c->arena.free(g->orig);
+    for (auto &kv : g->splits) {
+        c->arena.free(kv.second.heavy_v);
+        c->arena.free(kv.second.heavy_tptr);
+        c->arena.free(kv.second.task_e);
+    }
+    g->splits.clear();
+    return CC_OK;
+}
+
+// Algorithm 4 (neighbour-list partitioning): a vertex whose list is longer than
+// s gets ceil(deg / s) tasks of at most s neighbours; the tasks of one vertex
+// are contiguous so their partial rows are summed without atomics.
+cc_status ensure_split(Ctx *c, Graph *g, int64_t s, cudaStream_t st)
+{
+    if (g->splits.count(s)) return CC_OK;
+    Graph::Split sp;
+    sp.s = s;
+    std::vector<int64_t> te;
+    sp.h_heavy_tptr.push_back(0);
+    for (int64_t v = 0; v < g->n_act; v++) {
+        int64_t e0 = g->h_row_ptr[v], e1 = g->h_row_ptr[v + 1];
+        if (e1 - e0 <= s) continue;
+        sp.h_heavy_v.push_back((int32_t)v);
+        for (int64_t e = e0; e < e1; e += s) {
+            te.push_back(e);
+            te.push_back(std::min(e + s, e1));
+        }
+        sp.h_heavy_tptr.push_back((int64_t)te.size() / 2);
+    }
+    sp.H = (int64_t)sp.h_heavy_v.size();
+    sp.T = (int64_t)te.size() / 2;
+    sp.heavy_v = (int32_t *)c->arena.alloc(sizeof(int32_t) * std::max<int64_t>(sp.H, 1));
+    sp.heavy_tptr = (int64_t *)c->arena.alloc(sizeof(int64_t) * (sp.H + 1));
+    sp.task_e = (int64_t *)c->arena.alloc(sizeof(int64_t) * std::max<int64_t>(2 * sp.T, 2));
+    if (!sp.heavy_v || !sp.heavy_tptr || !sp.task_e) {
+        c->arena.free(sp.heavy_v);
+        c->arena.free(sp.heavy_tptr);
+        c->arena.free(sp.task_e);
+        return fail(CC_ERR_BUDGET, "task lists do not fit the HBM budget");
+    }
+    if (sp.H) {
+        CC_CUDA(cudaMemcpyAsync(sp.heavy_v, sp.h_heavy_v.data(), sizeof(int32_t) * sp.H, cudaMemcpyHostToDevice, st));
+        CC_CUDA(cudaMemcpyAsync(sp.task_e, te.data(), sizeof(int64_t) * te.size(), cudaMemcpyHostToDevice, st));
+    }
+    CC_CUDA(cudaMemcpyAsync(sp.heavy_tptr, sp.h_heavy_tptr.data(), sizeof(int64_t) * (sp.H + 1),
+                            cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaStreamSynchronize(st));
+    g->splits[s] = std::move(sp);
+    return CC_OK;
+}
+
+}  // namespace cc

@@ -1,0 +1,78 @@
+// kernels.cuh -- launch wrappers for the colour-coding DP kernels (sm_103a).
+//
+// Data layout in device memory (one "pass" processes B colourings at once):
+//   colours  col[v * B + b]                       uint8
+//   hist     hist[(v * B + b) * k + c]            uint32  (leaf gather, p = 1)
+//   tables   X[((v * B + b) * C + s) * L + limb]  uint64  (C = C(k, |T|) colex columns)
+// v runs over the active (non-isolated) vertices in the library's compact
+// numbering.  A "block" is a contiguous vertex range [v0, v1) whose working
+// rows (aggregates, chain intermediates) are stored at local row v - v0.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace cc {
+
+struct ColourParams {
+    uint64_t hj[64];  // F(F(seed) + j) for the colourings of the pass (b < B <= 64)
+};
+
+// per-pass parameters live in device memory so a captured graph can be replayed
+void launch_colour(cudaStream_t st, int64_t n_act, int B, int k, const int64_t *orig_id,
+                   const ColourParams *prm, uint8_t *col);
+
+void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const int64_t *row_ptr,
+                 const int32_t *col_idx, const uint8_t *col, uint32_t *hist);
+
+// agg[v - v0] = sum_{u in N(v)} X[u]  over rows of R values; light vertices only
+// (deg <= split), heavy ones go through tasks + reduce.
+void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                         const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
+                         int64_t R, uint64_t *agg);
+
+// tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
+void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
+                         const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
+                         int64_t R, uint64_t *partial);
+
+// heavy vertices [h0, h1) of the heavy list: agg[v - v0] = sum of their partial rows
+void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64_t v0, int64_t t0,
+                          const int32_t *heavy_v, const int64_t *heavy_tptr, const uint64_t *partial,
+                          int64_t R, uint64_t *agg);
+
+// combine kernels (Eq. 1 inner sum).  Rows: act C(k,a), agg C(k,p), out C(k,h); B per vertex.
+void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Ca,
+                            int64_t Cp, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
+                            const uint64_t *agg, uint64_t *out);
+// a = 1: act is the single vertex v with colour col(v)
+void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B,
+                           int k, int64_t Ch, int64_t Cp, const uint16_t *rm, const uint8_t *col,
+                           const void *agg, uint64_t *out);
+// p = 1: agg is the colour histogram of N(v)
+void launch_combine_hist(cudaStream_t st, int L, int64_t v0, int64_t nv, int B, int k, int64_t Ch,
+                         int64_t Ca, int h, const uint16_t *rm, const uint64_t *act,
+                         const uint32_t *hist, uint64_t *out);
+
+// totals[b] += sum_v root[v][b]  (root rows hold C(k,k) = 1 column)
+void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_t *root,
+                        uint64_t *scratch, int64_t scratch_ctas, uint64_t *totals);
+
+// samples: out[(b * n_s + i) * L] = root[sample_local[i]][b] for samples inside [v0, v1)
+void launch_sample_extract(cudaStream_t st, int L, int64_t n_s, const int64_t *sample_v,
+                           int64_t v0, int64_t v1, int B, const uint64_t *root, uint64_t *out);
+
+// homomorphism bound: H[v] *= sum_{u in N(v)} Hc[u]  (Hc == nullptr: all ones)
+void launch_hom_step(cudaStream_t st, int64_t n_act, const int64_t *row_ptr, const int32_t *col_idx,
+                     const double *Hc, double *H);
+void launch_fill_double(cudaStream_t st, int64_t n, double v, double *x);
+// out[0] = max, out[1] = sum (out must be zeroed)
+void launch_max_sum(cudaStream_t st, int64_t n, const double *x, double *out);
+
+// col_idx remap for the compact numbering: dst[e] = new_id[src[e]]
+void launch_remap(cudaStream_t st, int64_t nnz, const int32_t *src, const int32_t *new_id, int32_t *dst);
+
+int64_t reduce_scratch_ctas();
+
+}  // namespace cc

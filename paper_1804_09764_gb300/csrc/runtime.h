@@ -1,0 +1,199 @@
+// runtime.h -- context, graphs, templates, plan instances and the executor.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cc.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace cc {
+
+// thread-local error message; returns the status for `return fail(...)`
+cc_status fail(cc_status s, const std::string &msg);
+
+#define CC_CUDA(call)                                                                             \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return ::cc::fail(CC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+#define CC_TRY(expr)                      \
+    do {                                  \
+        cc_status s_ = (expr);            \
+        if (s_ != CC_OK) return s_;       \
+    } while (0)
+
+// Best-fit sub-allocator over one device allocation (256-byte aligned blocks).
+class Arena {
+public:
+    void init(char *base, uint64_t bytes);
+    // returns nullptr when no free block is large enough
+    void *alloc(uint64_t bytes);
+    void free(void *p);
+    uint64_t free_bytes() const { return free_total_; }
+    uint64_t largest_free() const;
+    uint64_t capacity() const { return cap_; }
+    char *base() const { return base_; }
+
+private:
+    char *base_ = nullptr;
+    uint64_t cap_ = 0, free_total_ = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> size
+    std::map<uint64_t, uint64_t> used_;  // offset -> size
+};
+
+struct Graph {
+    int64_t n = 0, n_act = 0, nnz = 0;
+    int64_t max_degree = 0;
+    // device (arena)
+    int64_t *row_ptr = nullptr;   // [n_act + 1]
+    int32_t *col_idx = nullptr;   // [nnz], compact ids
+    int64_t *orig = nullptr;      // [n_act] original id of each compact vertex
+    // host copies used for planning
+    std::vector<int64_t> h_row_ptr;
+    std::vector<int32_t> h_new_id;  // original id -> compact id or -1 (isolated)
+    // homomorphism bounds cache: canonical form -> (log2 max_v, log2 sum_v)
+    std::map<std::string, std::pair<double, double>> hom_cache;
+    // heavy-vertex task lists per split threshold
+    struct Split {
+        int64_t s = 0;
+        int32_t *heavy_v = nullptr;     // [H]
+        int64_t *heavy_tptr = nullptr;  // [H + 1]
+        int64_t *task_e = nullptr;      // [2 T]
+        std::vector<int32_t> h_heavy_v;
+        std::vector<int64_t> h_heavy_tptr;
+        int64_t H = 0, T = 0;
+    };
+    std::map<int64_t, Split> splits;
+    int in_use = 0;  // requests referencing this graph
+};
+
+struct Template {
+    int k = 0, root_req = -1;
+    std::vector<int32_t> edges;
+    int64_t aut = 1;
+};
+
+// A template planned against a graph with a batch size and width policy.
+struct PlanInstance {
+    TemplatePlan tp;
+    int64_t graph_id = 0, tmpl_id = 0;
+    int B = 1;
+    int width_bits = 0;     // 0 exact
+    bool exact = true;
+    int L_root = 1;
+    std::vector<int> chain_L;
+    int Lmax = 1;
+    int64_t V = 0;          // vertices per block
+    std::vector<std::pair<int64_t, int64_t>> blocks;
+    struct BlockHeavy { int64_t h0, h1, t0, t1; };
+    std::vector<BlockHeavy> heavy;
+    int64_t split = 1024;
+    int64_t max_tasks = 0;
+    // device constants (arena): rm tables per h, pair tables per (h, a)
+    void *consts = nullptr;
+    std::vector<uint16_t *> d_rm;               // [h]
+    std::map<std::pair<int, int>, uint32_t *> d_pairs;
+    // workspace layout (offsets from ws base)
+    uint64_t ws_bytes = 0;
+    uint64_t off_col = 0, off_hist = 0, off_act[2] = {0, 0}, off_agg = 0, off_partial = 0, off_root = 0,
+             off_scratch = 0, off_totals = 0, off_params = 0;
+    std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
+    // analytic figures
+    double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0;
+};
+
+enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_OTHER, K_KINDS };
+
+struct KernelTimer {
+    bool on = false;
+    int64_t launches[CC_KERNEL_KINDS] = {0};
+    double seconds[CC_KERNEL_KINDS] = {0};
+    double bytes[CC_KERNEL_KINDS] = {0};
+    int64_t total_launches = 0;
+    struct Pending { cudaEvent_t a, b; int kind; double bytes; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+struct Request;
+
+struct Ctx {
+    cc_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char *arena_base = nullptr;
+    bool own_arena = false;
+    Arena arena;
+    std::recursive_mutex mu;
+    int64_t next_id = 1;
+    std::map<int64_t, std::unique_ptr<Graph>> graphs;
+    std::map<int64_t, std::unique_ptr<Template>> templates;
+    KernelTimer timer;
+    std::atomic<int64_t> launches{0};
+    // serving
+    std::unique_ptr<struct Server> server;
+    Ctx();
+    ~Ctx();  // defined where Server is complete
+};
+
+// executor entry points
+cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                     cc_graph_id *out);
+cc_status graph_free(Ctx *c, Graph *g);
+cc_status ensure_split(Ctx *c, Graph *g, int64_t s, cudaStream_t st);
+
+struct CountJob {
+    uint64_t seed = 0;
+    int64_t first_iter = 0;
+    int32_t n_iter = 0;
+    int32_t width_bits = -1;
+    int32_t mom_groups = 1;
+    std::vector<int64_t> sample_vertices;  // original ids
+};
+
+// plan (with workspace sizing) for a count with n_iter colourings
+cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
+                    std::unique_ptr<PlanInstance> *out);
+void free_plan(Ctx *c, PlanInstance *p);
+
+// Runs passes [pass0, pass1) of a job on stream st using workspace ws.
+// Per pass: host params -> device, colour, hist, chains, reduce; totals/samples
+// copied to host_totals / host_samples (pinned) at pass offsets.
+cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int pass0, int pass1,
+                     cudaStream_t st, ColourParams *host_params, uint64_t *host_totals, uint64_t *host_samples,
+                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out);
+
+// Host post-processing: copies, estimate, median of means, writes caller buffers.
+cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
+                        const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
+                        uint64_t *sample_out, cc_result *res);
+
+cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
+                     uint64_t *maps, uint64_t *sample_out, cc_result *res);
+
+// serving (serve.cpp)
+cc_status serve_submit(Ctx *c, const cc_request *r, cc_req_id *out);
+cc_status serve_poll(Ctx *c, cc_req_id id, cc_result *res, uint64_t *counts, int32_t cap, bool wait,
+                     int64_t timeout_ns);
+cc_status serve_cancel(Ctx *c, cc_req_id id);
+cc_status serve_stats(Ctx *c, cc_serve_stats *out);
+void serve_shutdown(Ctx *c);
+
+uint64_t splitmix64_host(uint64_t state);
+
+}  // namespace cc

@@ -29,6 +29,17 @@ __all__ = [
 ]
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent difference)."""
+    a = np.sort(a)
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 class CSRGraph:
     """Undirected graph in symmetric CSR form."""
 
@@ -65,7 +76,7 @@ def _csr_from_unique_pairs(n: int, lo: np.ndarray, hi: np.ndarray, name: str) ->
     src = np.concatenate([lo, hi])
     dst = np.concatenate([hi, lo])
     key = src * n + dst
-    key.sort(kind="stable")
+    key.sort()
     src = key // n
     dst = (key - src * n).astype(np.int32)
     counts = np.bincount(src, minlength=n)
@@ -85,7 +96,7 @@ def csr_from_edges(n: int, edges, name: str = "") -> CSRGraph:
     e = e[e[:, 0] != e[:, 1]]
     lo = np.minimum(e[:, 0], e[:, 1])
     hi = np.maximum(e[:, 0], e[:, 1])
-    key = np.unique(lo * n + hi)
+    key = _sorted_unique(lo * n + hi)
     return _csr_from_unique_pairs(n, key // n, key % n, name)
 
 
@@ -104,10 +115,13 @@ def er_graph(n: int, avg_degree: float, seed: int) -> CSRGraph:
         ok = a != b
         a, b = a[ok], b[ok]
         drawn = np.concatenate([drawn, np.minimum(a, b) * n + np.maximum(a, b)])
-        _, first = np.unique(drawn, return_index=True)
-        if first.size >= m:
-            first.sort()
-            keys = np.sort(drawn[first[:m]])
+        order = np.argsort(drawn, kind="stable")
+        srt = drawn[order]
+        first = np.ones(srt.size, dtype=bool)
+        first[1:] = srt[1:] != srt[:-1]
+        first_pos = np.sort(order[first])          # draw positions of first occurrences
+        if first_pos.size >= m:
+            keys = np.sort(drawn[first_pos[:m]])
             break
     return _csr_from_unique_pairs(n, keys // n, keys % n, f"er_n{n}_d{avg_degree}_s{seed}")
 
@@ -122,32 +136,40 @@ def random_graph_gnp(n: int, p: float, seed: int) -> CSRGraph:
 
 def rmat_graph(scale: int, seed: int, edge_factor: int = 16,
                a: float = 0.57, b: float = 0.19, c: float = 0.19,
-               permute: bool = True, chunk: int = 1 << 23) -> CSRGraph:
-    """Seeded R-MAT graph on 2**scale vertices (d = 1 - a - b - c)."""
+               permute: bool = True, chunk: int = 1 << 24) -> CSRGraph:
+    """Seeded R-MAT graph on 2**scale vertices (d = 1 - a - b - c).
+
+    Each of the edge_factor * 2**scale samples picks, level by level, one of the
+    four quadrants with probabilities (a, b, c, d) from a uniform 32-bit draw.
+    """
+    if scale > 31:
+        raise ValueError("scale must be <= 31")
     n = 1 << scale
     total = edge_factor << scale
     rng = np.random.default_rng(seed)
-    t_ab = a + b
-    t_abc = a + b + c
+    two32 = float(1 << 32)
+    t_a = np.uint32(min(int(a * two32), (1 << 32) - 1))
+    t_ab = np.uint32(min(int((a + b) * two32), (1 << 32) - 1))
+    t_abc = np.uint32(min(int((a + b + c) * two32), (1 << 32) - 1))
     keys = []
     done = 0
     while done < total:
         cnt = min(chunk, total - done)
-        src = np.zeros(cnt, dtype=np.int64)
-        dst = np.zeros(cnt, dtype=np.int64)
+        src = np.zeros(cnt, dtype=np.uint32)
+        dst = np.zeros(cnt, dtype=np.uint32)
         for bit in range(scale):
-            r = rng.random(cnt)
-            down = r >= t_ab
-            right = ((r >= a) & (r < t_ab)) | (r >= t_abc)
-            src |= down.astype(np.int64) << bit
-            dst |= right.astype(np.int64) << bit
+            r = rng.integers(0, 1 << 32, size=cnt, dtype=np.uint32)
+            down = r >= t_ab                          # quadrants c, d
+            right = (r >= t_a) & (r < t_ab)           # quadrant b
+            right |= r >= t_abc                       # quadrant d
+            src |= down.astype(np.uint32) << np.uint32(bit)
+            dst |= right.astype(np.uint32) << np.uint32(bit)
         keep = src != dst
-        src, dst = src[keep], dst[keep]
-        lo = np.minimum(src, dst)
-        hi = np.maximum(src, dst)
-        keys.append(np.unique(lo * n + hi))
+        lo = np.minimum(src[keep], dst[keep]).astype(np.int64)
+        hi = np.maximum(src[keep], dst[keep]).astype(np.int64)
+        keys.append(_sorted_unique(lo * n + hi))
         done += cnt
-    key = np.unique(np.concatenate(keys)) if len(keys) > 1 else keys[0]
+    key = _sorted_unique(np.concatenate(keys)) if len(keys) > 1 else keys[0]
     lo = key >> scale
     hi = key & (n - 1)
     if permute:

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element
+by element, on the same seeded inputs.  Integer counts must be bit-exact; the
+FP64 estimate must agree to a relative 1e-12.
+
+Sizes are chosen so the oracle finishes in seconds while the GPU path still
+crosses several vertex blocks with a ragged tail, splits heavy neighbour lists
+into tasks, and runs several colouring passes with a ragged last pass."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_09764_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+EST_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1804_09764_gb300 import build as B
+    from paper_1804_09764_gb300 import cc
+
+    B.build()
+    c = cc.Context(budget_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+def make_ctx(**kw):
+    from paper_1804_09764_gb300 import cc
+
+    return cc.Context(budget_bytes=kw.pop("budget_bytes", 4 << 30), **kw)
+
+
+def oracle_maps(g, k, e, root, seed, js):
+    return [O.count_maps(g, k, e, root, seed=seed, j=j) for j in js]
+
+
+def check_counts(res, maps, k, aut, limbs):
+    M = 1 << (64 * limbs)
+    for j, m in enumerate(maps):
+        if res["exact"]:
+            assert res["counts"][j] == m // aut, f"colouring {j}"
+            assert m % aut == 0
+        else:
+            assert res["counts"][j] == m % M, f"colouring {j}"
+    if res["exact"] and maps:
+        est = [O.estimate(m // aut, k) for m in maps]
+        mean = math.fsum(est) / len(est)
+        assert res["estimate"] == pytest.approx(mean, rel=EST_RTOL, abs=1e-300)
+
+
+# ------------------------------------------------------------------ workload 1
+
+def test_er2000_p5_one_colouring(ctx):
+    # ER n=2000, d=8; P5; k=5; one colouring (the tiny plain-method workload)
+    g = gg.er_graph(2000, 8, seed=1)
+    k, e = gg.template_edges("P5")
+    gid = ctx.graph_load(g, validate=True)
+    for root in range(k):
+        tid = ctx.template_load(k, e, root)
+        res = ctx.count(gid, tid, seed=1, n_iter=1, want_maps=True)
+        maps = oracle_maps(g, k, e, root, 1, [0])
+        assert res["maps"] == maps
+        check_counts(res, maps, k, 2, res["limbs"])
+        ctx.template_free(tid)
+    ctx.graph_free(gid)
+
+
+# ------------------------------------------------------------------ R-MAT, several templates
+
+@pytest.mark.parametrize("name,scale,root,n_iter", [
+    ("caterpillar10", 11, 2, 5),
+    ("tree12", 10, 3, 2),
+    ("spider15", 9, 0, 1),
+])
+def test_rmat_templates_blocks_splits_batches(name, scale, root, n_iter):
+    g = gg.rmat_graph(scale, seed=scale)
+    k, e = gg.template_edges(name)
+    aut = O.automorphisms(k, e)
+    maps = oracle_maps(g, k, e, root, 7, range(n_iter))
+    # several tiles: 3 vertex blocks with a ragged tail, heavy lists split in tasks of 16,
+    # batches of 2 colourings with a ragged last pass
+    for kw in (dict(), dict(block_vertices=701, split_threshold=16, batch=2)):
+        c = make_ctx(**kw)
+        gid = c.graph_load(g)
+        tid = c.template_load(k, e, root)
+        res = c.count(gid, tid, seed=7, n_iter=n_iter, want_maps=True)
+        assert res["maps"] == [m % (1 << (64 * res["limbs"])) for m in maps]
+        check_counts(res, maps, k, aut, res["limbs"])
+        c.close()
+
+
+def test_partition_invariance_and_planner_root():
+    g = gg.rmat_graph(10, seed=5)
+    k, e = gg.template_edges("caterpillar10")
+    c = make_ctx(split_threshold=32)
+    gid = c.graph_load(g)
+    ref = O.count_maps(g, k, e, 0, seed=3, j=4)
+    for root in list(range(k)) + [-1]:
+        tid = c.template_load(k, e, root)
+        res = c.count(gid, tid, seed=3, n_iter=1, first_iter=4, want_maps=True)
+        assert res["maps"][0] == ref
+        c.template_free(tid)
+    c.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_trees(seed):
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(3, 10))
+    e = gg.prufer_tree(k, 77 + seed)
+    g = gg.rmat_graph(9, seed=100 + seed) if seed % 2 else gg.er_graph(700, 6, seed=seed)
+    root = int(rng.integers(0, k))
+    c = make_ctx(batch=3, split_threshold=24)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, root)
+    res = c.count(gid, tid, seed=seed, n_iter=4, want_maps=True)
+    maps = oracle_maps(g, k, e, root, seed, range(4))
+    check_counts(res, maps, k, O.automorphisms(k, e), res["limbs"])
+    c.close()
+
+
+# ------------------------------------------------------------------ integer widths
+
+@pytest.mark.parametrize("width", [64, 128, 192, 256])
+def test_forced_width_residues(width):
+    g = gg.rmat_graph(10, seed=2)
+    k, e = gg.template_edges("tree12")
+    c = make_ctx(width_bits=width)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 3)
+    res = c.count(gid, tid, seed=9, n_iter=1)
+    m = O.count_maps(g, k, e, 3, seed=9, j=0)
+    assert res["exact"] == 0 and res["limbs"] == width // 64
+    assert res["counts"][0] == m % (1 << width)
+    c.close()
+
+
+def test_wide_exact_counts_star_on_star():
+    # counts above 2^128: star template on K_{1,4000}, k = 14
+    k = 14
+    e = [(0, i) for i in range(1, k)]
+    g = gg.star_graph(4000)
+    c = make_ctx(split_threshold=64)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 0)
+    res = c.count(gid, tid, seed=5, n_iter=2, want_maps=True)
+    maps = oracle_maps(g, k, e, 0, 5, range(2))
+    assert res["limbs"] >= 3
+    assert res["maps"] == maps
+    assert max(maps).bit_length() > 128
+    c.close()
+
+
+# ------------------------------------------------------------------ per-vertex outputs
+
+def test_sampled_vertices_match_oracle_per_vertex():
+    g = gg.rmat_graph(10, seed=8)
+    k, e = gg.template_edges("caterpillar10")
+    _, pv = O.count_maps(g, k, e, 2, seed=4, j=1, per_vertex=True)
+    c = make_ctx(block_vertices=333, split_threshold=20)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 2)
+    sample = list(range(0, g.n, 7)) + [g.n - 1]
+    res = c.count(gid, tid, seed=4, n_iter=1, first_iter=1, sample_vertices=sample)
+    assert res["samples"][0] == [pv[v] for v in sample]
+    c.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_cases():
+    c = make_ctx()
+    # empty graph and graph without edges
+    for g in (gg.csr_from_edges(0, np.zeros((0, 2))), gg.csr_from_edges(5, np.zeros((0, 2)))):
+        gid = c.graph_load(g)
+        for k, e in ((1, []), (2, [(0, 1)]), (4, [(0, 1), (1, 2), (2, 3)])):
+            tid = c.template_load(k, e)
+            res = c.count(gid, tid, seed=1, n_iter=2)
+            assert res["counts"] == [g.n if k == 1 else 0] * 2
+        c.graph_free(gid)
+    # k = 1 counts every vertex, isolated ones included; k = 2 counts colourful edges
+    g = gg.csr_from_edges(10, [(0, 1), (1, 2), (5, 6)])
+    gid = c.graph_load(g)
+    tid = c.template_load(1, [])
+    assert c.count(gid, tid, seed=1, n_iter=1)["counts"] == [10]
+    tid = c.template_load(2, [(0, 1)])
+    res = c.count(gid, tid, seed=11, n_iter=3)
+    assert res["counts"] == [O.count_maps(g, 2, [(0, 1)], 0, seed=11, j=j) // 2 for j in range(3)]
+    # template larger than any component: zero
+    tid = c.template_load(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
+    assert c.count(gid, tid, seed=1, n_iter=1)["counts"] == [0]
+    c.close()
+
+
+def test_bad_inputs_raise():
+    from paper_1804_09764_gb300 import cc
+
+    c = make_ctx()
+    rp = np.array([0, 1, 1], dtype=np.int64)
+    with pytest.raises(cc.CCError) as ei:   # asymmetric
+        c.graph_load_csr(rp, np.array([1], dtype=np.int32), validate=True)
+    assert ei.value.status == -2
+    with pytest.raises(cc.CCError) as ei:   # self-loop
+        c.graph_load_csr(np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), validate=True)
+    assert ei.value.status == -2
+    with pytest.raises(cc.CCError) as ei:   # not a tree
+        c.template_load(3, [(0, 1), (1, 0)])
+    assert ei.value.status == -3
+    g = gg.er_graph(100, 4, seed=1)
+    gid = c.graph_load(g)
+    tid = c.template_load(5, gg.template_edges("P5")[1])
+    with pytest.raises(cc.CCError) as ei:   # capacity
+        c.count(gid, tid, seed=1, n_iter=1, limbs_capacity=0)
+    c.close()
+
+
+def test_budget_refusal():
+    from paper_1804_09764_gb300 import cc
+
+    g = gg.rmat_graph(12, seed=1)
+    c = make_ctx(budget_bytes=8 << 20)
+    gid = c.graph_load(g)
+    tid = c.template_load(*gg.template_edges("tree12"), 3)
+    with pytest.raises(cc.CCError) as ei:
+        c.count(gid, tid, seed=1, n_iter=1)
+    assert ei.value.status == -5
+    c.close()

@@ -1,0 +1,105 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports every
+symbol of include/cc.h, the planner's cost model reproduces Table 4, the
+library's automorphism count (AHU canonical forms) agrees with the oracle's
+backtracking count, and the input generators behave."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_09764_gb300 import build as B
+from paper_1804_09764_gb300 import cc
+from paper_1804_09764_gb300 import graphgen as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return cc.load_library()
+
+
+def header_functions():
+    with open(os.path.join(ROOT, "include", "cc.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function(lib):
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(cc.EXPORTED) <= set(names)
+    assert lib.cc_version().decode().startswith("cc-gb300")
+
+
+def test_status_strings(lib):
+    for code, name in cc.STATUS.items():
+        assert lib.cc_status_string(code).decode() == name
+
+
+def test_table4_cost_model():
+    # Table 4 (Section 4.1): memory = sum C(k,|T_i|), computation = sum C(k,|T_i|) C(|T_i|,|T_i'|)
+    rows = []
+    with open(os.path.join(GOLDEN, "table4_cost.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line.split())
+    assert len(rows) == 3
+    for name, k, mem, comp, edges in rows:
+        e = [tuple(int(x) for x in p.split("-")) for p in edges.split(",")]
+        assert cc.cc_template_cost(int(k), e, 0, 0) == (int(mem), int(comp)), name
+
+
+def test_automorphisms_agree_with_oracle():
+    for k in range(1, 13):
+        for seed in range(5):
+            e = gg.prufer_tree(k, 1000 + seed)
+            assert cc.cc_template_automorphisms(k, e) == O.automorphisms(k, e)
+    for name in ("P5", "caterpillar10", "tree12", "spider15"):
+        k, e = gg.template_edges(name)
+        assert cc.cc_template_automorphisms(k, e) == O.automorphisms(k, e)
+    # stars: (k-1)! (not enumerated by the oracle)
+    for k in (10, 14, 16):
+        assert cc.cc_template_automorphisms(k, [(0, i) for i in range(1, k)]) == int(np.prod(range(1, k)))
+
+
+def test_template_validation(lib):
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_template_cost(3, [(0, 1), (0, 1)], 0)
+    assert ei.value.status == -3
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_template_cost(4, [(0, 1), (2, 3), (0, 1)], 0)
+    assert ei.value.status == -3
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_template_cost(17, [(i, i + 1) for i in range(16)], 0)
+    assert ei.value.status == -4
+
+
+def test_generators_are_deterministic_and_simple():
+    a = gg.rmat_graph(10, seed=3)
+    b = gg.rmat_graph(10, seed=3)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col_idx, b.col_idx)
+    for g in (a, gg.er_graph(500, 8, seed=2), gg.cycle_graph(7), gg.complete_graph(6), gg.star_graph(9)):
+        assert g.row_ptr[0] == 0 and g.row_ptr[-1] == g.col_idx.size
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        assert not np.any(src == g.col_idx)
+        fwd = set(zip(src.tolist(), g.col_idx.tolist()))
+        assert len(fwd) == g.col_idx.size
+        assert all((v, u) in fwd for u, v in fwd)
+    er = gg.er_graph(2000, 8, seed=1)
+    assert er.m == 8000
+
+
+def test_prufer_trees_are_trees():
+    for k in range(2, 17):
+        e = gg.prufer_tree(k, k)
+        assert len(e) == k - 1
+        assert O.automorphisms(k, e) >= 1  # raises if not a tree
