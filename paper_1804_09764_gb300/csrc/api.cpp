@@ -277,7 +277,7 @@ cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out)
     if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
-    static const char *names[CC_KERNEL_KINDS] = {"colour", "hist", "gather", "combine", "reduce", "fused", "other", "-"};
+    static const char *names[CC_KERNEL_KINDS] = {"colour", "hist", "gather", "combine", "reduce", "fused", "select", "combine_hist"};
     std::memset(out, 0, sizeof *out);
     for (int i = 0; i < CC_KERNEL_KINDS; i++) {
         out->name[i] = names[i];

@@ -426,12 +426,15 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     out = (uint64_t *)W(p->off_act[si & 1]);
                 if (s.src_chain < 0) {
                     const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
-                    Ln.begin(K_COMBINE);
-                    if (s.a == 1)
+                    if (s.a == 1) {
+                        Ln.begin(K_SELECT);
                         launch_combine_select(st, L, true, v0, nv, B, k, Ch, k, p->d_rm[s.h], col, hrow, out);
-                    else
+                        Ln.end(1, (double)nv * B * (Ch * 8.0 * L + 4.0 * k + 1));
+                    } else {
+                        Ln.begin(K_CHIST);
                         launch_combine_hist(st, L, v0, nv, B, k, Ch, cur_cols, s.h, p->d_rm[s.h], cur, hrow, out);
-                    Ln.end(1, (double)nv * B * Ch * 8 * L);
+                        Ln.end(1, (double)nv * B * ((Ch + cur_cols) * 8.0 * L + 4.0 * k));
+                    }
                 } else {
                     const int Ls = p->chain_L[s.src_chain];
                     const int64_t Cp = binom(k, s.p);
@@ -454,13 +457,16 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         }
                         Ln.end(nl, bytes);
                     }
-                    Ln.begin(K_COMBINE);
-                    if (s.a == 1)
+                    if (s.a == 1) {
+                        Ln.begin(K_SELECT);
                         launch_combine_select(st, L, false, v0, nv, B, k, Ch, Cp, p->d_rm[s.h], col, agg, out);
-                    else
+                        Ln.end(1, (double)nv * B * ((Ch + Cp) * 8.0 * L + 1));
+                    } else {
+                        Ln.begin(K_COMBINE);
                         launch_combine_generic(st, L, nv, B, Ch, cur_cols, Cp, binom(s.h, s.a), p->d_pairs.at({s.h, s.a}),
                                                cur, agg, out);
-                    Ln.end(1, (double)nv * B * Ch * 8 * L);
+                        Ln.end(1, (double)nv * B * (Ch + cur_cols + Cp) * 8.0 * L);
+                    }
                 }
                 cur = out;
                 cur_cols = Ch;

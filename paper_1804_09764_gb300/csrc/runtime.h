@@ -116,7 +116,7 @@ struct PlanInstance {
     double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0;
 };
 
-enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_OTHER, K_KINDS };
+enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_SELECT, K_CHIST, K_KINDS };
 
 struct KernelTimer {
     bool on = false;
