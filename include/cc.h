@@ -198,6 +198,24 @@ typedef struct cc_kernel_stats {
 cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out);
 cc_status cc_kernel_stats_reset(cc_ctx *ctx);
 
+/*
+ * Eq. 1's neighbour sum for one count table on its own (the table-gather step):
+ *   agg[v] = sum_{u in N(v)} X[u]   for every v in [0, n)
+ * where a row holds `values` integers of `limbs` 64-bit limbs, added modulo
+ * 2^(64*limbs).  All pointers are device memory:
+ *   row_ptr [n+1] int64, col_idx [row_ptr[n]] int32 (any CSR, symmetric or not),
+ *   X, agg  [n][values][limbs] uint64 (may not overlap).
+ * Neighbour lists longer than split_threshold (0: 1024) are cut into tasks of at
+ * most that many neighbours (Algorithm 4); the tasks' partial rows and the task
+ * list are scratch carved from the context's arena and released before return.
+ * Runs on the context's stream and synchronises it.
+ * Errors: CC_ERR_INVALID_ARG (bad sizes, limbs outside 1..4), CC_ERR_BUDGET
+ * (scratch does not fit the arena), CC_ERR_CUDA.
+ */
+cc_status cc_table_gather(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                          const uint64_t *X, uint64_t *agg, int64_t values, int32_t limbs,
+                          int32_t split_threshold);
+
 /* ------------------------------------------------------------------ serving */
 
 /* One count request (same arithmetic as cc_count_ex). */

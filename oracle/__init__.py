@@ -168,6 +168,29 @@ def median_of_means(estimates, t: int) -> float:
     return 0.5 * (means[t // 2 - 1] + means[t // 2])
 
 
+def neighbour_sum(graph, X: np.ndarray, limbs: int) -> np.ndarray:
+    """Eq. 1's inner sum over u in N(v) of a count table, on its own:
+    out[v] = sum_{u in N(v)} X[u], each value an integer of `limbs` 64-bit limbs
+    (least significant first) added modulo 2^(64*limbs).  X: uint64
+    [n][values][limbs]; plain Python integers."""
+    n, values, L = X.shape
+    assert L == limbs
+    M = 1 << (64 * limbs)
+    vals = [[sum(int(X[u, c, i]) << (64 * i) for i in range(L)) for c in range(values)] for u in range(n)]
+    out = np.zeros_like(X)
+    for v in range(n):
+        acc = [0] * values
+        for u in graph.neighbours(v):
+            row = vals[int(u)]
+            for c in range(values):
+                acc[c] += row[c]
+        for c in range(values):
+            x = acc[c] % M
+            for i in range(L):
+                out[v, c, i] = (x >> (64 * i)) & ((1 << 64) - 1)
+    return out
+
+
 def run(graph, k: int, edges, seed: int, n_iter: int, root: int = 0, first_iter: int = 0):
     """Algorithm 1 for colourings first_iter .. first_iter+n_iter-1.
 

@@ -33,7 +33,7 @@ EXPORTED = [
     "cc_graph_load_csr", "cc_graph_free", "cc_template_load", "cc_template_free", "cc_count",
     "cc_count_ex", "cc_plan_info_get", "cc_kernel_stats_get", "cc_kernel_stats_reset", "cc_submit",
     "cc_poll", "cc_wait", "cc_cancel", "cc_serve_stats_get", "cc_template_cost",
-    "cc_template_automorphisms", "cc_version",
+    "cc_template_automorphisms", "cc_version", "cc_table_gather",
 ]
 
 
@@ -132,6 +132,7 @@ def load_library(path: str = LIB_PATH):
         "cc_template_cost": (I32, [I32, P, I32, I32, P, P]),
         "cc_template_automorphisms": (I32, [I32, P, P]),
         "cc_version": (ctypes.c_char_p, []),
+        "cc_table_gather": (I32, [P, I64, P, P, P, P, I64, I32, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -331,6 +332,13 @@ class Context:
 
     def kernel_stats_reset(self):
         _check(self._lib.cc_kernel_stats_reset(self._h))
+
+    def table_gather(self, row_ptr, col_idx, X, agg, values: int, limbs: int, split: int = 0):
+        """cc_table_gather on torch device tensors (row_ptr int64, col_idx int32,
+        X / agg uint64-compatible int64 tensors of n*values*limbs)."""
+        n = row_ptr.numel() - 1
+        _check(self._lib.cc_table_gather(self._h, n, row_ptr.data_ptr(), col_idx.data_ptr(), X.data_ptr(),
+                                         agg.data_ptr(), values, limbs, split))
 
     # -- serving
     def submit(self, gid: int, tid: int, seed: int, n_iter: int, first_iter: int = 0) -> int:

@@ -328,6 +328,16 @@ cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *au
     return CC_OK;
 }
 
+cc_status cc_table_gather(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
+                          uint64_t *agg, int64_t values, int32_t limbs, int32_t split_threshold)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return table_gather(c, n, row_ptr, col_idx, X, agg, values, limbs, split_threshold);
+}
+
 cc_status cc_submit(cc_ctx *ctx, const cc_request *req, cc_req_id *out)
 {
     if (!ctx || !req || !out) return fail(CC_ERR_INVALID_ARG, "NULL argument");

@@ -189,4 +189,70 @@ cc_status ensure_split(Ctx *c, Graph *g, int64_t s, cudaStream_t st)
     return CC_OK;
 }
 
+// Standalone table gather (cc_table_gather): the light / task / reduce kernels of
+// the counting path on caller-provided device rows, task list and partial rows
+// in the arena.
+cc_status table_gather(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
+                       uint64_t *agg, int64_t values, int32_t limbs, int32_t split)
+{
+    if (n < 0 || n >= (int64_t(1) << 31) || values < 1 || limbs < 1 || limbs > 4 || split < 0)
+        return fail(CC_ERR_INVALID_ARG, "bad n, values, limbs or split_threshold");
+    if (n == 0) return CC_OK;
+    if (!row_ptr || !col_idx || !X || !agg) return fail(CC_ERR_INVALID_ARG, "NULL device pointer");
+    const int64_t s = split > 0 ? split : 1024;
+    cudaStream_t st = c->stream;
+    std::vector<int64_t> rp(n + 1);
+    CC_CUDA(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    CC_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> hv;
+    std::vector<int64_t> tptr{0}, te;
+    for (int64_t v = 0; v < n; v++) {
+        int64_t e0 = rp[v], e1 = rp[v + 1];
+        if (e1 < e0) return fail(CC_ERR_INVALID_ARG, "row_ptr decreases");
+        if (e1 - e0 <= s) continue;
+        hv.push_back((int32_t)v);
+        for (int64_t e = e0; e < e1; e += s) {
+            te.push_back(e);
+            te.push_back(std::min(e + s, e1));
+        }
+        tptr.push_back((int64_t)te.size() / 2);
+    }
+    const int64_t H = (int64_t)hv.size(), T = (int64_t)te.size() / 2;
+    const uint64_t row_bytes = (uint64_t)values * limbs * 8;
+    int32_t *d_hv = nullptr;
+    int64_t *d_tptr = nullptr, *d_te = nullptr;
+    uint64_t *d_part = nullptr;
+    if (T > 0) {
+        d_hv = (int32_t *)c->arena.alloc(sizeof(int32_t) * H);
+        d_tptr = (int64_t *)c->arena.alloc(sizeof(int64_t) * (H + 1));
+        d_te = (int64_t *)c->arena.alloc(sizeof(int64_t) * 2 * T);
+        d_part = (uint64_t *)c->arena.alloc(row_bytes * T);
+        if (!d_hv || !d_tptr || !d_te || !d_part) {
+            c->arena.free(d_hv);
+            c->arena.free(d_tptr);
+            c->arena.free(d_te);
+            c->arena.free(d_part);
+            return fail(CC_ERR_BUDGET, "task scratch does not fit the arena");
+        }
+        CC_CUDA(cudaMemcpyAsync(d_hv, hv.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, st));
+        CC_CUDA(cudaMemcpyAsync(d_tptr, tptr.data(), sizeof(int64_t) * (H + 1), cudaMemcpyHostToDevice, st));
+        CC_CUDA(cudaMemcpyAsync(d_te, te.data(), sizeof(int64_t) * 2 * T, cudaMemcpyHostToDevice, st));
+    }
+    launch_gather_light(st, limbs, limbs, 0, n, s, row_ptr, col_idx, X, values, agg);
+    c->launches++;
+    if (T > 0) {
+        launch_gather_tasks(st, limbs, limbs, 0, T, col_idx, d_te, X, values, d_part);
+        launch_gather_reduce(st, limbs, 0, H, 0, 0, d_hv, d_tptr, d_part, values, agg);
+        c->launches += 2;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    c->arena.free(d_hv);
+    c->arena.free(d_tptr);
+    c->arena.free(d_te);
+    c->arena.free(d_part);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, std::string("table gather: ") + cudaGetErrorString(e));
+    return CC_OK;
+}
+
 }  // namespace cc

@@ -196,4 +196,7 @@ void serve_shutdown(Ctx *c);
 
 uint64_t splitmix64_host(uint64_t state);
 
+cc_status table_gather(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
+                       uint64_t *agg, int64_t values, int32_t limbs, int32_t split);
+
 }  // namespace cc

@@ -230,3 +230,24 @@ def test_budget_refusal():
         c.count(gid, tid, seed=1, n_iter=1)
     assert ei.value.status == -5
     c.close()
+
+
+# ------------------------------------------------------------------ table gather on its own
+
+@pytest.mark.parametrize("limbs,split", [(1, 0), (2, 8), (3, 5), (4, 16)])
+def test_table_gather_matches_oracle_neighbour_sum(limbs, split):
+    import torch
+
+    g = gg.rmat_graph(9, seed=31)
+    values = 7
+    rng = np.random.default_rng(limbs)
+    X = rng.integers(0, 2 ** 64, size=(g.n, values, limbs), dtype=np.uint64)
+    expect = O.neighbour_sum(g, X, limbs)
+    c = make_ctx()
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    Xt = torch.from_numpy(X.view(np.int64)).cuda()
+    A = torch.full_like(Xt, -1)
+    c.table_gather(rp, ci, Xt, A, values, limbs, split)
+    assert np.array_equal(A.cpu().numpy().view(np.uint64), expect)
+    c.close()
