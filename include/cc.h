@@ -216,6 +216,35 @@ cc_status cc_table_gather(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const 
                           const uint64_t *X, uint64_t *agg, int64_t values, int32_t limbs,
                           int32_t split_threshold);
 
+/*
+ * cc_table_gather without any device allocation.  The paper has no counterpart:
+ * this is a library service for callers that cannot allocate device memory (a
+ * framework that owns all device memory through its own pool, a latency-bound
+ * loop where cudaMalloc/cudaFree and their implicit synchronisation are not
+ * acceptable, a process with a fixed memory budget).
+ *   Computes agg[v] = sum_{u in N(v)} X[u] exactly like cc_table_gather (same
+ *   kernels, same results) with the same argument meaning; no context needed.
+ *   All pointers are device memory on the calling thread's current device;
+ *   stream is a cudaStream_t (NULL: the legacy default stream).
+ *   Scratch: the task list and the tasks' partial rows live in a 64 MiB
+ *   file-scope device array that every GPU loading this library holds until the
+ *   process exits.  It fits at most (64 MiB - ~1.3 KiB) / (28 + values*limbs*8)
+ *   split tasks; larger inputs return CC_ERR_CAPACITY before any gather kernel
+ *   runs (raise split_threshold to need fewer tasks).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.
+ *   The call synchronises `stream` once (to read the task count) and returns
+ *   with the gather kernels queued on `stream`.  All calls share the array and
+ *   each call rewrites what it reads, so nothing needs clearing between calls,
+ *   but calls whose kernels overlap on the GPU race on the array: serialise them.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: CC_ERR_INVALID_ARG, CC_ERR_CAPACITY, CC_ERR_CUDA.
+ */
+cc_status cc_table_gather_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                  const uint64_t *X, uint64_t *agg, int64_t values, int32_t limbs,
+                                  int32_t split_threshold, void *stream);
+
 /* ------------------------------------------------------------------ serving */
 
 /* One count request (same arithmetic as cc_count_ex). */

@@ -33,7 +33,7 @@ EXPORTED = [
     "cc_graph_load_csr", "cc_graph_free", "cc_template_load", "cc_template_free", "cc_count",
     "cc_count_ex", "cc_plan_info_get", "cc_kernel_stats_get", "cc_kernel_stats_reset", "cc_submit",
     "cc_poll", "cc_wait", "cc_cancel", "cc_serve_stats_get", "cc_template_cost",
-    "cc_template_automorphisms", "cc_version", "cc_table_gather",
+    "cc_template_automorphisms", "cc_version", "cc_table_gather", "cc_table_gather_noalloc",
 ]
 
 
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH):
         "cc_template_automorphisms": (I32, [I32, P, P]),
         "cc_version": (ctypes.c_char_p, []),
         "cc_table_gather": (I32, [P, I64, P, P, P, P, I64, I32, I32]),
+        "cc_table_gather_noalloc": (I32, [I64, P, P, P, P, I64, I32, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -183,6 +184,17 @@ def cc_template_automorphisms(k: int, edges) -> int:
     e = _edges_array(k, edges)
     _check(lib.cc_template_automorphisms(k, _ptr(e), ctypes.byref(a)))
     return a.value
+
+
+def cc_table_gather_noalloc(row_ptr, col_idx, X, agg, values: int, limbs: int, split: int = 0,
+                            stream: int = 0):
+    """cc_table_gather_noalloc on torch device tensors (no context, no device
+    allocation by the library); returns after the gather kernels are queued on
+    ``stream`` (a raw cudaStream_t handle, 0 = legacy default stream)."""
+    lib = load_library()
+    n = row_ptr.numel() - 1
+    _check(lib.cc_table_gather_noalloc(n, row_ptr.data_ptr(), col_idx.data_ptr(), X.data_ptr(), agg.data_ptr(),
+                                       values, limbs, split, stream or None))
 
 
 # ------------------------------------------------------------------ context
