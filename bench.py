@@ -41,6 +41,8 @@ WORKLOADS = {
     "rmat20_caterpillar10": dict(graph=("rmat", 20, 20), template="caterpillar10", root=2, n_iter=64,
                                  budget=100 << 30),
     "rmat22_tree12": dict(graph=("rmat", 22, 22), template="tree12", root=-1, n_iter=16, budget=100 << 30),
+    # small case of the same kernels for profiler captures (tables ~4 GB, above L2)
+    "rmat18_tree12": dict(graph=("rmat", 18, 18), template="tree12", root=-1, n_iter=1, budget=16 << 30),
     "rmat24_spider15": dict(graph=("rmat", 24, 24), template="spider15", root=0, n_iter=4, budget=150 << 30),
 }
 DEFAULT = "rmat22_tree12"
@@ -50,6 +52,24 @@ def make_graph(spec):
     if spec[0] == "er":
         return gg.er_graph(spec[1], spec[2], seed=spec[3])
     return gg.rmat_graph(spec[1], seed=spec[2])
+
+
+def replica_first_iter(rank: int, world: int, step: int, n_iter: int) -> int:
+    """Colourings are independent units (Algorithm 1's outer loop), so replicas
+    shard them: step `step` of rank `rank` runs colourings
+    [(step * world + rank) * n_iter, ... + n_iter) -- disjoint across ranks and
+    steps, no data exchange."""
+    return (step * world + rank) * n_iter
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank time over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -197,6 +217,74 @@ def plan_updates_host(g, k, e, root):
     return U
 
 
+def run_serving(args):
+    """Continuous-batching serving run: resident R-MAT graphs (scales 16..max)
+    plus an Erdos-Renyi graph (n = 1M, degree 16); requests with Poisson
+    arrivals, each a uniform labelled tree (Pruefer) with k in 5..12 and 1..16
+    colourings.  Reports p50/p99 latency (arrival to result) and throughput, and
+    the same requests run one after another through cc_count (plain path)."""
+    import torch
+
+    from paper_1804_09764_gb300 import build as B
+    from paper_1804_09764_gb300 import cc
+
+    B.build()
+    rng = np.random.default_rng(2024)
+    scales = list(range(16, args.serve_max_scale + 1))
+    graphs = [gg.rmat_graph(sc, seed=sc) for sc in scales] + [gg.er_graph(1 << 20, 16, seed=7)]
+    budget = min(int(args.budget_gb * (1 << 30)) if args.budget_gb else 200 << 30,
+                 int(torch.cuda.mem_get_info(0)[0] * 0.9))
+    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
+    gids = [ctx.graph_load(g) for g in graphs]
+    reqs = []
+    t = 0.0
+    for i in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        k = int(rng.integers(5, 13))
+        e = gg.prufer_tree(k, 10_000 + i)
+        reqs.append(dict(at=t, g=int(rng.integers(0, len(graphs))), k=k, e=e, n_iter=int(rng.integers(1, 17)),
+                         seed=int(rng.integers(0, 2 ** 40))))
+    for r in reqs:
+        r["tid"] = ctx.template_load(r["k"], r["e"])
+    # updates per request (same U definition as the counting metric)
+    for r in reqs:
+        r["U"] = plan_updates_host(graphs[r["g"]], r["k"], r["e"], 0) * r["n_iter"]
+    # plain path: one request after another through cc_count
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        ctx.count(gids[r["g"]], r["tid"], seed=r["seed"], n_iter=r["n_iter"])
+    plain_s = time.perf_counter() - t0
+    # served: submit at arrival times, collect results
+    start = time.perf_counter()
+    ids = []
+    lat = []
+    for r in reqs:
+        now = time.perf_counter() - start
+        if r["at"] > now:
+            time.sleep(r["at"] - now)
+        ids.append((ctx.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"]), r))
+    for rid, r in ids:
+        ctx.wait(rid, r["n_iter"], timeout_s=3600)
+    served_s = time.perf_counter() - start
+    st = ctx.serve_stats()
+    U = sum(r["U"] for r in reqs)
+    line = {"metric": "served_p99_latency_s", "value": st["p99_latency_s"], "unit": "s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": served_s * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64/u128/u192", "data": "synthetic",
+            "config": {"workload": "serve", "graphs": [g.name for g in graphs], "requests": args.requests,
+                       "rate_per_s": args.rate, "slots": args.serve_slots, "k": "5..12", "colourings": "1..16",
+                       "arrival_span_s": reqs[-1]["at"]},
+            "serving": {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+                        "mean_latency_s": st["mean_latency_s"], "completed": st["completed"],
+                        "requests_per_s": args.requests / served_s, "updates_per_s": U / served_s,
+                        "busy_s": st["busy_seconds"], "admissions_deferred": st["admissions_deferred"]},
+            "plain_sequential": {"seconds": plain_s, "requests_per_s": args.requests / plain_s,
+                                 "updates_per_s": U / plain_s}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,6 +298,15 @@ def main():
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--gather-mode", type=int, default=1,
+                    help="1 warp gather (default), 0 bulk-copy (TMA) ring, 2 warp 16-byte vectors, 3 group, "
+                         "4 warp + L2 prefetch")
+    ap.add_argument("--budget-gb", type=float, default=0, help="HBM arena size (0: the workload's)")
+    ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-max-scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
@@ -219,6 +316,10 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.serve:
+        if rank == 0:
+            run_serving(args)
         return
 
     import torch
@@ -239,16 +340,17 @@ def main():
     g = make_graph(wl["graph"])
     gen_s = time.time() - t0
     k, e = gg.template_edges(wl["template"])
-    budget = min(wl["budget"], int(torch.cuda.mem_get_info(local)[0] * 0.9))
+    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else wl["budget"]
+    budget = min(budget, int(torch.cuda.mem_get_info(local)[0] * 0.9))
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
-                     block_vertices=args.block)
+                     block_vertices=args.block, gather_mode=args.gather_mode)
     gid = ctx.graph_load(g)
     tid = ctx.template_load(k, e, wl["root"])
     info = ctx.plan_info(gid, tid)
     n_iter = wl["n_iter"]
 
     def step(i):
-        return ctx.count(gid, tid, seed=12345, n_iter=n_iter, first_iter=(rank * 1000 + i) * n_iter)
+        return ctx.count(gid, tid, seed=12345, n_iter=n_iter, first_iter=replica_first_iter(rank, world, i, n_iter))
 
     for i in range(args.warmup):
         step(i)
@@ -269,9 +371,7 @@ def main():
     ks = ctx.kernel_stats()
     elapsed = dev_s
     if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, device=f"cuda:{local}")
     U = info["updates_per_colouring"] * n_iter * args.steps * world
     value = U / elapsed
 
@@ -323,7 +423,9 @@ def main():
                    "workspace_gb": info["workspace_bytes"] / 1e9, "l2": "inputs larger than L2",
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
-                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3)},
+                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3),
+                   "gather": {0: "bulk-copy (TMA)", 1: "warp per row", 2: "warp (16-byte vectors)",
+                              3: "group (row per 32-256 threads)", 4: "warp + L2 prefetch"}[args.gather_mode]},
         "hbm_frac_step": info["algorithmic_bytes_per_colouring"] * n_iter * args.steps / elapsed / 1e9 / peak,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -49,7 +49,7 @@ class cc_options(ctypes.Structure):
                 ("split_threshold", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("block_vertices", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("autotune", ctypes.c_int32), ("max_slots", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class cc_result(ctypes.Structure):
@@ -209,7 +209,8 @@ class Context:
 
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
-                 fused: int = 0, autotune: int = 0, max_slots: int = 4, timing: int = 0, stream=None):
+                 fused: int = 0, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
+                 stream=None):
         import torch
 
         lib = load_library()
@@ -238,6 +239,7 @@ class Context:
         opt.autotune = autotune
         opt.max_slots = max_slots
         opt.timing = timing
+        opt.gather_mode = gather_mode
         torch.cuda.synchronize(device)
         h = ctypes.c_void_p()
         _check(lib.cc_create(ctypes.byref(h), ctypes.byref(opt)))

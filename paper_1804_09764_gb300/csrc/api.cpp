@@ -59,6 +59,7 @@ void cc_default_options(cc_options *opt)
     opt->autotune = 0;
     opt->max_slots = 4;
     opt->timing = 0;
+    opt->gather_mode = 1;
 }
 
 cc_status cc_create(cc_ctx **out, const cc_options *opt)
@@ -122,6 +123,7 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt)
     }
     c->arena.init(c->arena_base, bytes);
     c->timer.on = c->opt.timing != 0;
+    init_kernel_attributes();
     *out = reinterpret_cast<cc_ctx *>(c);
     return CC_OK;
 }
@@ -135,6 +137,7 @@ cc_status cc_destroy(cc_ctx *ctx)
         std::lock_guard<std::recursive_mutex> lk(c->mu);
         cudaSetDevice(c->device);
         cudaStreamSynchronize(c->stream);
+        evict_plans(c);
         for (auto &kv : c->graphs) graph_free(c, kv.second.get());
         c->graphs.clear();
         for (auto e : c->timer.pool) cudaEventDestroy(e);
@@ -169,6 +172,7 @@ cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g)
     if (it->second->in_use) return fail(CC_ERR_INVALID_ARG, "graph is used by a queued or running request");
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    evict_plans(c, g, -1);
     graph_free(c, it->second.get());
     c->graphs.erase(it);
     return CC_OK;
@@ -199,7 +203,9 @@ cc_status cc_template_free(cc_ctx *ctx, cc_template_id t)
     if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
-    if (!c->templates.erase(t)) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    if (!c->templates.count(t)) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    evict_plans(c, -1, t);
+    c->templates.erase(t);
     return CC_OK;
 }
 

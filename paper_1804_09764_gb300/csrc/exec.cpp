@@ -46,10 +46,10 @@ cc_status hom_bounds(Ctx *c, Graph *g, const TemplatePlan &tp, cudaStream_t st, 
     }
     if (!all) {
         std::vector<double *> H(nc, nullptr);
-        double *red = (double *)c->arena.alloc(16);
+        double *red = (double *)arena_alloc(c, 16);
         bool ok = red != nullptr;
         for (int i = 0; i < nc && ok; i++) {
-            H[i] = (double *)c->arena.alloc(sizeof(double) * std::max<int64_t>(g->n_act, 1));
+            H[i] = (double *)arena_alloc(c, sizeof(double) * std::max<int64_t>(g->n_act, 1));
             ok = H[i] != nullptr;
         }
         if (!ok) {
@@ -84,7 +84,8 @@ int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(
 
 struct Layout {
     uint64_t bytes = 0;
-    uint64_t off_col, off_hist, off_act[2], off_agg, off_partial, off_root, off_scratch, off_totals, off_params;
+    uint64_t off_col, off_hist, off_act[2], off_agg, off_partial, off_root, off_scratch, off_totals, off_params,
+        off_err;
     std::vector<uint64_t> off_table;
     int64_t max_tasks = 0;
     std::vector<std::pair<int64_t, int64_t>> blocks;
@@ -120,7 +121,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     for (int i = 0; i < nc; i++) {
         const auto &C = tp.chains[i];
         if (C.is_root) continue;
-        uint64_t sz = rup((uint64_t)n * B * binom(k, C.size) * 8 * p.chain_L[i]);
+        uint64_t sz = rup((uint64_t)n * B * col_stride(binom(k, C.size)) * 8 * p.chain_L[i]);
         int start = i, end = C.last_consumer;
         // lowest offset not overlapping any live placed table
         std::vector<std::pair<uint64_t, uint64_t>> busy;
@@ -148,8 +149,8 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     for (auto &C : tp.chains)
         for (size_t si = 0; si < C.steps.size(); si++) {
             const auto &s = C.steps[si];
-            if (si + 1 < C.steps.size()) maxAct = std::max<int64_t>(maxAct, binom(k, s.h));
-            if (s.src_chain >= 0) maxP = std::max<int64_t>(maxP, binom(k, s.p));
+            if (si + 1 < C.steps.size()) maxAct = std::max<int64_t>(maxAct, col_stride(binom(k, s.h)));
+            if (s.src_chain >= 0) maxP = std::max<int64_t>(maxP, col_stride(binom(k, s.p)));
             else need_hist = true;
         }
     const int Lm = p.Lmax;
@@ -163,6 +164,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     Lo.off_scratch = take((uint64_t)reduce_scratch_ctas() * B * 8 * p.L_root);
     Lo.off_totals = take((uint64_t)B * 8 * p.L_root);
     Lo.off_params = take(sizeof(ColourParams));
+    Lo.off_err = take(256);
     Lo.bytes = cur;
     return Lo;
 }
@@ -242,6 +244,13 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     }
     if (!found) return fail(CC_ERR_BUDGET, "plan does not fit the HBM budget (largest free block " +
                                                std::to_string(room >> 20) + " MiB)");
+    {
+        auto tm = c->tuned_modes.find(std::make_tuple(gid, tid, p->B));
+        if (tm != c->tuned_modes.end()) {
+            p->site_mode = tm->second;
+            p->tuned = true;
+        }
+    }
     p->ws_bytes = Lo.bytes;
     p->off_col = Lo.off_col;
     p->off_hist = Lo.off_hist;
@@ -253,6 +262,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     p->off_scratch = Lo.off_scratch;
     p->off_totals = Lo.off_totals;
     p->off_params = Lo.off_params;
+    p->off_err = Lo.off_err;
     p->off_table = Lo.off_table;
     p->blocks = Lo.blocks;
     p->heavy = Lo.heavy;
@@ -263,7 +273,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     std::vector<std::pair<int, int>> need_pairs;
     for (auto &C : tp.chains)
         for (auto &s : C.steps)
-            if (s.a >= 2 && s.src_chain >= 0) need_pairs.push_back({s.h, s.a});
+            if (s.a >= 2) need_pairs.push_back({s.h, s.a});  // p = 1 steps use the (h, h-1) table
     std::sort(need_pairs.begin(), need_pairs.end());
     need_pairs.erase(std::unique(need_pairs.begin(), need_pairs.end()), need_pairs.end());
     uint64_t cbytes = 0;
@@ -273,7 +283,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
         pt.push_back(T.pairs(hp.first, hp.second));
         cbytes += rup(pt.back().size() * 4);
     }
-    p->consts = c->arena.alloc(std::max<uint64_t>(cbytes, 256));
+    p->consts = arena_alloc(c, std::max<uint64_t>(cbytes, 256));
     if (!p->consts) return fail(CC_ERR_BUDGET, "no room for colour-set tables");
     char *cp = (char *)p->consts;
     p->d_rm.assign(k + 1, nullptr);
@@ -382,7 +392,7 @@ static void drain_timer(Ctx *c)
 }
 
 static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st, const int64_t *d_samples,
-                             int64_t n_samples, uint64_t *d_samples_out)
+                             int64_t n_samples, uint64_t *d_samples_out, bool tune = false)
 {
     Graph *g = c->graphs.at(p->graph_id).get();
     const TemplatePlan &tp = p->tp;
@@ -412,64 +422,113 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
             const int64_t v0 = p->blocks[bi].first, v1 = p->blocks[bi].second, nv = v1 - v0;
             const auto &hv = p->heavy[bi];
             const uint64_t *cur = nullptr;
-            int64_t cur_cols = k;
+            int64_t cur_stride = k;
             uint64_t *root_rows = (uint64_t *)W(p->off_root);
             for (size_t si = 0; si < C.steps.size(); si++) {
                 const Step &s = C.steps[si];
                 const bool last = si + 1 == C.steps.size();
                 const int64_t Ch = binom(k, s.h);
+                // root rows hold one column and are never gathered: no padding
+                const int64_t Chs = (last && C.is_root) ? 1 : col_stride(Ch);
                 uint64_t *out;
                 if (last)
                     out = C.is_root ? root_rows
-                                    : (uint64_t *)W(p->off_table[ci]) + (uint64_t)v0 * B * Ch * L;
+                                    : (uint64_t *)W(p->off_table[ci]) + (uint64_t)v0 * B * Chs * L;
                 else
                     out = (uint64_t *)W(p->off_act[si & 1]);
                 if (s.src_chain < 0) {
                     const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
-                        launch_combine_select(st, L, true, v0, nv, B, k, Ch, k, p->d_rm[s.h], col, hrow, out);
+                        launch_combine_select(st, L, true, v0, nv, B, k, Ch, Chs, k, p->d_rm[s.h], col, hrow, out);
                         Ln.end(1, (double)nv * B * (Ch * 8.0 * L + 4.0 * k + 1));
                     } else {
                         Ln.begin(K_CHIST);
-                        launch_combine_hist(st, L, v0, nv, B, k, Ch, cur_cols, s.h, p->d_rm[s.h], cur, hrow, out);
-                        Ln.end(1, (double)nv * B * ((Ch + cur_cols) * 8.0 * L + 4.0 * k));
+                        launch_combine_hist(st, L, nv, B, k, Ch, Chs, cur_stride, s.h, p->d_pairs.at({s.h, s.a}), cur,
+                                            hrow, out);
+                        Ln.end(1, (double)nv * B * ((Ch + binom(k, s.a)) * 8.0 * L + 4.0 * k));
                     }
                 } else {
                     const int Ls = p->chain_L[s.src_chain];
-                    const int64_t Cp = binom(k, s.p);
-                    const int64_t R = (int64_t)B * Cp;
+                    const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
+                    const int64_t R = (int64_t)B * Cps;
                     const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
                     if (!s.reuse_agg) {
                         // algorithmic bytes of this gather: neighbour rows + CSR + aggregate write
                         double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
-                        double bytes = e_blk * R * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * R * 8.0 * L;
+                        double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Cp * 8.0 * L;
                         Ln.begin(K_GATHER);
-                        launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
-                        int nl = 1;
-                        if (hv.t1 > hv.t0) {
-                            uint64_t *part = (uint64_t *)W(p->off_partial);
-                            launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
-                            launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R,
-                                                 agg);
-                            nl += 2;
+                        int *err = (int *)W(p->off_err);
+                        auto run_gather = [&](int gm) {
+                            const bool bulk = gm == 0 && bulk_gather_ok(Ls, R);
+                            const bool group = gm == 3 && vec_gather_ok(Ls, R);
+                            const bool vec = !bulk && !group && (gm == 0 || gm == 2) && vec_gather_ok(Ls, R);
+                            if (bulk)
+                                launch_gather_light_bulk(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, g->nnz,
+                                                         X, R, agg, err);
+                            else if (group)
+                                launch_gather_light_group(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R,
+                                                          agg);
+                            else if (vec)
+                                launch_gather_light_vec(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
+                            else
+                                launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
+                                                    gm == 4);
+                            int n = 1;
+                            if (hv.t1 > hv.t0) {
+                                uint64_t *part = (uint64_t *)W(p->off_partial);
+                                if (bulk)
+                                    launch_gather_tasks_bulk(st, Ls, L, hv.t0, hv.t1, g->col_idx, g->nnz, sp.task_e, X,
+                                                             R, part, err);
+                                else if (group)
+                                    launch_gather_tasks_group(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R,
+                                                              part);
+                                else if (vec)
+                                    launch_gather_tasks_vec(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
+                                else
+                                    launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
+                                                        gm == 4);
+                                launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
+                                                     R, agg);
+                                n += 2;
+                            }
+                            return n;
+                        };
+                        int nl = 0;
+                        const auto site = std::make_pair((int)ci, (int)si);
+                        if (tune) {
+                            // every variant computes the same sums; the last one run leaves agg
+                            for (int gm : {0, 2, 3, 4, 1}) {  // the default (1) last
+                                if ((gm == 0 && !bulk_gather_ok(Ls, R)) || ((gm == 2 || gm == 3) && !vec_gather_ok(Ls, R)))
+                                    continue;
+                                PlanInstance::Trial tr{(int)ci, (int)si, gm, nullptr, nullptr};
+                                cudaEventCreate(&tr.a);
+                                cudaEventCreate(&tr.b);
+                                cudaEventRecord(tr.a, st);
+                                nl += run_gather(gm);
+                                cudaEventRecord(tr.b, st);
+                                p->trials.push_back(tr);
+                            }
+                        } else {
+                            auto it = p->site_mode.find(site);
+                            nl += run_gather(it != p->site_mode.end() ? it->second : c->opt.gather_mode);
                         }
                         Ln.end(nl, bytes);
                     }
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
-                        launch_combine_select(st, L, false, v0, nv, B, k, Ch, Cp, p->d_rm[s.h], col, agg, out);
+                        launch_combine_select(st, L, false, v0, nv, B, k, Ch, Chs, Cps, p->d_rm[s.h], col, agg, out);
                         Ln.end(1, (double)nv * B * ((Ch + Cp) * 8.0 * L + 1));
                     } else {
                         Ln.begin(K_COMBINE);
-                        launch_combine_generic(st, L, nv, B, Ch, cur_cols, Cp, binom(s.h, s.a), p->d_pairs.at({s.h, s.a}),
-                                               cur, agg, out);
-                        Ln.end(1, (double)nv * B * (Ch + cur_cols + Cp) * 8.0 * L);
+                        launch_combine_generic(st, L, nv, B, Ch, Chs, cur_stride, Cps, binom(s.h, s.a),
+                                               p->d_pairs.at({s.h, s.a}), cur, agg, out);
+                        Ln.end(1, (double)nv * B * (Ch + binom(k, s.a) + Cp) * 8.0 * L);
                     }
                 }
                 cur = out;
-                cur_cols = Ch;
+                cur_stride = Chs;
             }
             if (C.is_root) {
                 Ln.begin(K_REDUCE);
@@ -488,9 +547,62 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     return CC_OK;
 }
 
+// Capture one pass (colour .. root reduce) as a CUDA graph; launch counters are
+// restored because capturing launches nothing.
+static cc_status capture_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st, CachedPlan *cp)
+{
+    const int64_t l0 = c->launches.load();
+    KernelTimer saved = c->timer;
+    CC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cc_status rc = launch_pass(c, p, ws, st, nullptr, 0, nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cp->launches_per_pass = c->launches.load() - l0;
+    c->launches = l0;
+    for (int i = 0; i < CC_KERNEL_KINDS; i++) c->timer.launches[i] = saved.launches[i];
+    c->timer.total_launches = saved.total_launches;
+    if (rc != CC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&cp->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cp->gexec = nullptr;
+        return fail(CC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return CC_OK;
+}
+
+// After a tuning pass: per gather site, the variant with the least summed time.
+static cc_status finish_tuning(Ctx *c, PlanInstance *p, cudaStream_t st)
+{
+    CC_CUDA(cudaStreamSynchronize(st));
+    std::map<std::pair<int, int>, std::map<int, double>> t;
+    for (auto &tr : p->trials) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, tr.a, tr.b) == cudaSuccess) t[{tr.chain, tr.step}][tr.mode] += ms;
+        cudaEventDestroy(tr.a);
+        cudaEventDestroy(tr.b);
+    }
+    cudaGetLastError();
+    p->trials.clear();
+    for (auto &site : t) {
+        int best = c->opt.gather_mode;
+        double bt = 1e300;
+        for (auto &m : site.second)
+            if (m.second < bt) bt = m.second, best = m.first;
+        p->site_mode[site.first] = best;
+    }
+    p->tuned = true;
+    c->tuned_modes[std::make_tuple(p->graph_id, p->tmpl_id, p->B)] = p->site_mode;
+    return CC_OK;
+}
+
 cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int pass0, int pass1,
                      cudaStream_t st, ColourParams *host_params, uint64_t *host_totals, uint64_t *host_samples,
-                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out)
+                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out, CachedPlan *graph)
 {
     const int B = p->B;
     for (int ps = pass0; ps < pass1; ps++) {
@@ -499,7 +611,16 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
         for (int b = 0; b < B; b++)
             hp.hj[b] = splitmix64_host(fs + (uint64_t)(job.first_iter + (int64_t)ps * B + b));
         CC_CUDA(cudaMemcpyAsync(ws + p->off_params, &hp, sizeof(ColourParams), cudaMemcpyHostToDevice, st));
-        CC_TRY(launch_pass(c, p, ws, st, d_samples, n_samples, d_samples_out));
+        const bool tune = c->opt.autotune && !p->tuned;
+        if (graph && !graph->gexec && !tune && n_samples == 0) CC_TRY(capture_pass(c, p, ws, st, graph));
+        if (graph && graph->gexec && !tune && n_samples == 0) {
+            CC_CUDA(cudaGraphLaunch(graph->gexec, st));
+            c->launches += graph->launches_per_pass;
+            c->timer.total_launches += graph->launches_per_pass;
+        } else {
+            CC_TRY(launch_pass(c, p, ws, st, d_samples, n_samples, d_samples_out, tune));
+            if (tune) CC_TRY(finish_tuning(c, p, st));
+        }
         CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * B * p->L_root, ws + p->off_totals,
                                 (size_t)B * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
         if (n_samples > 0)
@@ -664,29 +785,52 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     if (t->k == 1 || g->n_act == 0 || job.n_iter == 0)
         return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res);
     cudaStream_t st = c->stream;
-    std::unique_ptr<PlanInstance> p;
-    CC_TRY(make_plan(c, gid, tid, job.n_iter, width, st, &p));
+    const int bcap = std::max(1, std::min({c->opt.batch > 0 ? c->opt.batch : 16, job.n_iter, 64}));
+    const auto key = std::make_tuple(gid, tid, bcap, width);
+    CachedPlan *cp = nullptr;
+    auto it = c->plan_cache.find(key);
+    if (it != c->plan_cache.end()) {
+        cp = &it->second;
+    } else {
+        std::unique_ptr<PlanInstance> np;
+        cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &np);
+        if (rc == CC_ERR_BUDGET && !c->plan_cache.empty()) {
+            evict_plans(c);
+            rc = make_plan(c, gid, tid, job.n_iter, width, st, &np);
+        }
+        if (rc != CC_OK) return rc;
+        char *ws = (char *)c->arena.alloc(np->ws_bytes);
+        if (!ws && !c->plan_cache.empty()) {
+            evict_plans(c);
+            ws = (char *)c->arena.alloc(np->ws_bytes);
+        }
+        if (!ws) {
+            free_plan(c, np.get());
+            return fail(CC_ERR_BUDGET, "workspace does not fit the HBM budget");
+        }
+        CachedPlan &slot = c->plan_cache[key];
+        slot.p = std::move(np);
+        slot.ws = ws;
+        cp = &slot;
+    }
+    cp->last_use = ++c->use_clock;
+    PlanInstance *p = cp->p.get();
     struct Cleanup {
         Ctx *c;
-        PlanInstance *p;
-        char *ws = nullptr;
         int64_t *ds = nullptr;
         uint64_t *dso = nullptr;
         void *hp = nullptr, *ht = nullptr, *hs = nullptr;
         ~Cleanup()
         {
             cudaStreamSynchronize(c->stream);
-            c->arena.free(ws);
             c->arena.free(ds);
             c->arena.free(dso);
             if (hp) cudaFreeHost(hp);
             if (ht) cudaFreeHost(ht);
             if (hs) cudaFreeHost(hs);
-            free_plan(c, p);
         }
-    } cl{c, p.get()};
-    cl.ws = (char *)c->arena.alloc(p->ws_bytes);
-    if (!cl.ws) return fail(CC_ERR_BUDGET, "workspace does not fit the HBM budget");
+    } cl{c};
+    char *ws = cp->ws;
     const int B = p->B;
     const int npass = (job.n_iter + B - 1) / B;
     const int64_t ns = (int64_t)job.sample_vertices.size();
@@ -697,7 +841,7 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
             cv[s] = (ov >= 0 && ov < g->n) ? g->h_new_id[ov] : -1;
         }
         cl.ds = (int64_t *)c->arena.alloc(8 * ns);
-        cl.dso = (uint64_t *)c->arena.alloc((uint64_t)8 * ns * B * p->L_root);
+        cl.dso = (uint64_t *)c->arena.alloc((uint64_t)8 * ns * B * p->L_root);  // (plan in use: no eviction)
         if (!cl.ds || !cl.dso) return fail(CC_ERR_BUDGET, "no room for sampled vertices");
         CC_CUDA(cudaMemcpyAsync(cl.ds, cv.data(), 8 * ns, cudaMemcpyHostToDevice, st));
         CC_CUDA(cudaMemsetAsync(cl.dso, 0, (size_t)8 * ns * B * p->L_root, st));
@@ -709,9 +853,10 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     CC_CUDA(cudaEventCreate(&e0));
     CC_CUDA(cudaEventCreate(&e1));
     int64_t l0 = c->launches.load();
+    CC_CUDA(cudaMemsetAsync(ws + p->off_err, 0, 256, st));
     CC_CUDA(cudaEventRecord(e0, st));
-    cc_status rc = run_passes(c, p.get(), cl.ws, job, 0, npass, st, (ColourParams *)cl.hp, (uint64_t *)cl.ht,
-                              (uint64_t *)cl.hs, cl.ds, ns, cl.dso);
+    cc_status rc = run_passes(c, p, ws, job, 0, npass, st, (ColourParams *)cl.hp, (uint64_t *)cl.ht,
+                              (uint64_t *)cl.hs, cl.ds, ns, cl.dso, (c->opt.use_cuda_graph && !c->timer.on) ? cp : nullptr);
     CC_CUDA(cudaEventRecord(e1, st));
     CC_CUDA(cudaStreamSynchronize(st));
     float ms = 0;
@@ -719,15 +864,54 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CC_OK) return rc;
+    int kerr = 0;
+    CC_CUDA(cudaMemcpy(&kerr, ws + p->off_err, sizeof kerr, cudaMemcpyDeviceToHost));
+    if (kerr) return fail(CC_ERR_TIMEOUT, "a gather kernel wait ran out of time (code " + std::to_string(kerr) + ")");
     if (res) {
         res->device_seconds = ms * 1e-3;
         res->kernel_launches = c->launches.load() - l0;
     }
-    rc = finish_counts(c, p.get(), g, job, (const uint64_t *)cl.ht, (const uint64_t *)cl.hs, counts, cap, maps,
+    rc = finish_counts(c, p, g, job, (const uint64_t *)cl.ht, (const uint64_t *)cl.hs, counts, cap, maps,
                        sample_out, res);
     if (res)
         res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     return rc;
+}
+
+void *arena_alloc(Ctx *c, uint64_t bytes)
+{
+    void *p = c->arena.alloc(bytes);
+    if (!p && !c->plan_cache.empty()) {
+        evict_plans(c);
+        p = c->arena.alloc(bytes);
+    }
+    return p;
+}
+
+void evict_plans(Ctx *c, int64_t gid, int64_t tid)
+{
+    cudaStreamSynchronize(c->stream);
+    for (auto it = c->tuned_modes.begin(); it != c->tuned_modes.end();) {
+        if ((gid >= 0 && std::get<0>(it->first) == gid) || (tid >= 0 && std::get<1>(it->first) == tid))
+            it = c->tuned_modes.erase(it);
+        else
+            ++it;
+    }
+    for (auto it = c->plan_cache.begin(); it != c->plan_cache.end();) {
+        const bool hit = (gid < 0 && tid < 0) || std::get<0>(it->first) == gid || std::get<1>(it->first) == tid;
+        if (!hit) {
+            ++it;
+            continue;
+        }
+        if (it->second.gexec) cudaGraphExecDestroy(it->second.gexec);
+        for (auto &tr : it->second.p->trials) {
+            cudaEventDestroy(tr.a);
+            cudaEventDestroy(tr.b);
+        }
+        c->arena.free(it->second.ws);
+        free_plan(c, it->second.p.get());
+        it = c->plan_cache.erase(it);
+    }
 }
 
 }  // namespace cc

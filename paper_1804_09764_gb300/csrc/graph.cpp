@@ -95,7 +95,7 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
     g->n_act = (int64_t)orig.size();
     g->nnz = nnz;
 
-    auto A = [&](uint64_t bytes) { return c->arena.alloc(bytes); };
+    auto A = [&](uint64_t bytes) { return arena_alloc(c, bytes); };
     g->row_ptr = (int64_t *)A(sizeof(int64_t) * (g->n_act + 1));
     g->col_idx = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
     g->orig = (int64_t *)A(sizeof(int64_t) * std::max<int64_t>(g->n_act, 1));
@@ -169,9 +169,9 @@ cc_status ensure_split(Ctx *c, Graph *g, int64_t s, cudaStream_t st)
     }
     sp.H = (int64_t)sp.h_heavy_v.size();
     sp.T = (int64_t)te.size() / 2;
-    sp.heavy_v = (int32_t *)c->arena.alloc(sizeof(int32_t) * std::max<int64_t>(sp.H, 1));
-    sp.heavy_tptr = (int64_t *)c->arena.alloc(sizeof(int64_t) * (sp.H + 1));
-    sp.task_e = (int64_t *)c->arena.alloc(sizeof(int64_t) * std::max<int64_t>(2 * sp.T, 2));
+    sp.heavy_v = (int32_t *)arena_alloc(c, sizeof(int32_t) * std::max<int64_t>(sp.H, 1));
+    sp.heavy_tptr = (int64_t *)arena_alloc(c, sizeof(int64_t) * (sp.H + 1));
+    sp.task_e = (int64_t *)arena_alloc(c, sizeof(int64_t) * std::max<int64_t>(2 * sp.T, 2));
     if (!sp.heavy_v || !sp.heavy_tptr || !sp.task_e) {
         c->arena.free(sp.heavy_v);
         c->arena.free(sp.heavy_tptr);

@@ -68,11 +68,20 @@ __global__ void hist_kernel(int64_t v0, int64_t v1, int B, int k, const int64_t 
     }
 }
 
+// Bulk prefetch of a contiguous range into L2 (no registers, no completion
+// tracking): the row of a neighbour is requested whole as soon as its id is
+// known, so the chunked loads that follow mostly hit L2.  Range and address
+// are multiples of 16 bytes (rows have an even number of 8-byte limbs).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.
 // Lane `lane` owns values base + q*32 + lane, q < VPT; the neighbour ids are
 // fetched 32 at a time and broadcast with shuffles; two neighbours are loaded
 // before adding so 2*VPT loads are in flight per lane.
-template <int Ls, int Ld, int VPT>
+template <int Ls, int Ld, int VPT, bool PF = false>
 __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
                                            const uint64_t *__restrict__ X, int64_t R,
                                            uint64_t *__restrict__ out_row, int lane)
@@ -84,6 +93,8 @@ __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, 
         for (int64_t e = e0; e < e1; e += 32) {
             const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
             const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+            if (PF && base == 0 && R > 32 * VPT && lane < cnt && (R * Ls) % 2 == 0)
+                prefetch_l2(X + (int64_t)myu * R * Ls, (uint32_t)(R * Ls * 8));
             int t = 0;
             for (; t + 2 <= cnt; t += 2) {
                 const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
@@ -126,7 +137,465 @@ __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, 
     }
 }
 
-template <int Ls, int Ld, int VPT>
+// ---------------------------------------------------------------- bulk-copy gather
+//
+// Persistent CTAs (one per SM) move whole neighbour-row segments into shared
+// memory with cp.async.bulk (TMA), completion tracked by mbarriers, so a few
+// hundred KB per SM are in flight with almost no registers.  Warp kBulkConsumers
+// (one elected lane) produces: for each work item (a light vertex, or a task of
+// a split neighbour list) and each column chunk it walks the neighbour list and
+// issues one bulk copy per neighbour into a ring of NS slots.  The consumer
+// warps add each staged segment into register accumulators (thread t owns values
+// t + q * 256 of the chunk) and free the slot; after the item's last neighbour
+// they store the summed chunk.  Every wait is bounded: on timeout the kernel
+// records an error code, stops issuing, waits (bounded) for the copies it has
+// in flight and returns.
+constexpr int kBulkConsumers = 16;                // consumer warps
+constexpr int kBulkThreads = (kBulkConsumers + 1) * 32;
+constexpr int kBulkMaxStages = 96;
+constexpr int64_t kBulkSmemBytes = 192 * 1024;    // stage ring
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false (and *err set) if the phase did not complete in time
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct BulkItems {
+    // mode 0: light vertices [v0, v1) with deg <= split, out row = v - v0
+    // mode 1: tasks [t0, t1) with ranges task_e, out row = t - t0
+    int mode;
+    int64_t v0, v1, split;
+    const int64_t *row_ptr;
+    int64_t t0, t1;
+    const int64_t *task_e;
+    int64_t nnz;  // length of col_idx
+};
+
+// this CTA's item range: vertex ranges balanced by neighbour count, task ranges by count
+__device__ __forceinline__ void bulk_item_range(const BulkItems &it, int64_t *a, int64_t *b)
+{
+    const int64_t G = gridDim.x, g = blockIdx.x;
+    if (it.mode == 1) {
+        const int64_t n = it.t1 - it.t0, per = (n + G - 1) / G;
+        *a = it.t0 + min(n, g * per);
+        *b = it.t0 + min(n, (g + 1) * per);
+        return;
+    }
+    const int64_t E0 = it.row_ptr[it.v0], E1 = it.row_ptr[it.v1], E = E1 - E0;
+    auto first_at = [&](int64_t target) {  // first v in [v0, v1] with row_ptr[v] >= target
+        int64_t lo = it.v0, hi = it.v1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (it.row_ptr[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    *a = (g == 0) ? it.v0 : first_at(E0 + (E * g) / G);
+    *b = (g == G - 1) ? it.v1 : first_at(E0 + (E * (g + 1)) / G);
+}
+
+// neighbour range of item i (one coalesced load per lane for 32 items at once)
+__device__ __forceinline__ void bulk_item_load(const BulkItems &it, int64_t i, int64_t *e0, int64_t *e1)
+{
+    if (it.mode == 1) {
+        *e0 = it.task_e[2 * i];
+        *e1 = it.task_e[2 * i + 1];
+    } else {
+        *e0 = it.row_ptr[i];
+        *e1 = it.row_ptr[i + 1];
+    }
+}
+
+template <int Ls, int Ld, int UPT>
+__global__ void __launch_bounds__(kBulkThreads, 1)
+gather_bulk_kernel(BulkItems it, const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
+                   uint64_t *__restrict__ out, int NS, int *err)
+{
+    static_assert(Ls == 1 || Ls == 2, "16-byte units hold whole values only for 1 or 2 limbs");
+    constexpr int VPU = 2 / Ls;                                // values per 16-byte unit
+    constexpr int NCT = kBulkConsumers * 32;                   // consumer threads
+    // units per chunk and per stage: one chunk covers short rows whole, so a
+    // slot is only as large as the row segment it holds
+    const int64_t CHU = min((int64_t)NCT * UPT, R * Ls / 2);
+    extern __shared__ __align__(128) unsigned char bulk_smem[];
+    __shared__ __align__(8) uint64_t full_bar[kBulkMaxStages], empty_bar[kBulkMaxStages];
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t units = R * Ls / 2;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], kBulkConsumers);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t ia, ib;
+    bulk_item_range(it, &ia, &ib);
+    ulonglong2 *stage = reinterpret_cast<ulonglong2 *>(bulk_smem);
+    const ulonglong2 *Xv = reinterpret_cast<const ulonglong2 *>(X);
+    const bool light = it.mode == 0;
+
+    if (warp == kBulkConsumers) {
+        // ---------------- producer warp: lane 0 issues, all lanes fetch ids
+        int slot = 0;
+        uint32_t phase = 0;
+        int64_t issued = 0;
+        bool ok = true;
+        int64_t wbase = -64;  // window of 32 neighbour ids held one per lane
+        int32_t wval = 0;
+        for (int64_t ig = ia; ig < ib && ok; ig += 32) {
+            const int nin = (ib - ig < 32) ? (int)(ib - ig) : 32;
+            int64_t la = 0, lb = 0;
+            if (lane < nin) bulk_item_load(it, ig + lane, &la, &lb);
+            for (int j = 0; j < nin && ok; j++) {
+                const int64_t e0 = __shfl_sync(0xffffffffu, la, j), e1 = __shfl_sync(0xffffffffu, lb, j);
+                if (light && e1 - e0 > it.split) continue;
+                for (int64_t cu0 = 0; cu0 < units && ok; cu0 += CHU) {
+                    const uint32_t bytes = (uint32_t)(min(CHU, units - cu0) * 16);
+                    for (int64_t e = e0; e < e1; e++) {
+                        if (e < wbase || e >= wbase + 32) {
+                            wbase = e;
+                            wval = (wbase + lane < it.nnz) ? col_idx[wbase + lane] : 0;
+                        }
+                        const int64_t u = __shfl_sync(0xffffffffu, wval, (int)(e - wbase));
+                        int good = 1;
+                        if (lane == 0) {
+                            good = mbar_wait(&empty_bar[slot], phase ^ 1u, err, 1) && !*((volatile int *)&abort_flag);
+                            if (good) {
+                                mbar_expect_tx(&full_bar[slot], bytes);
+                                bulk_g2s(stage + (int64_t)slot * CHU, Xv + u * units + cu0, bytes, &full_bar[slot]);
+                            }
+                        }
+                        if (!__shfl_sync(0xffffffffu, good, 0)) {
+                            ok = false;
+                            break;
+                        }
+                        issued++;
+                        if (++slot == NS) {
+                            slot = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) {
+            abort_flag = 1;
+            // drain: wait (bounded) for the last copy issued into each slot; slots are
+            // used round-robin, so slot s received issued / NS + (s < issued % NS) copies
+            for (int s = 0; s < NS; s++) {
+                const int64_t cnt = issued / NS + (s < issued % NS ? 1 : 0);
+                if (cnt > 0) mbar_wait(&full_bar[s], (uint32_t)((cnt - 1) & 1), err, 3);
+            }
+        }
+    } else {
+        // ---------------- consumer warps: thread t owns units t + q * NCT of a chunk
+        const int t = threadIdx.x;
+        int slot = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t ig = ia; ig < ib && ok; ig += 32) {
+            const int nin = (ib - ig < 32) ? (int)(ib - ig) : 32;
+            int64_t la = 0, lb = 0;
+            if (lane < nin) bulk_item_load(it, ig + lane, &la, &lb);
+            for (int j = 0; j < nin && ok; j++) {
+                const int64_t e0 = __shfl_sync(0xffffffffu, la, j), e1 = __shfl_sync(0xffffffffu, lb, j);
+                if (light && e1 - e0 > it.split) continue;
+                const int64_t orow = (ig + j) - (light ? it.v0 : it.t0);
+                uint64_t *dst = out + orow * R * Ld;
+                for (int64_t cu0 = 0; cu0 < units && ok; cu0 += CHU) {
+                    const int64_t nun = min(CHU, units - cu0);
+                    Wide<Ld> acc[UPT][VPU];
+#pragma unroll
+                    for (int q = 0; q < UPT; q++)
+#pragma unroll
+                        for (int h = 0; h < VPU; h++) wzero(acc[q][h]);
+                    for (int64_t e = e0; e < e1; e++) {
+                        // every lane waits on the barrier itself (acquire of the bulk-copy data)
+                        const int good = mbar_wait(&full_bar[slot], phase, err, 2) && !*((volatile int *)&abort_flag);
+                        if (!__all_sync(0xffffffffu, good)) {
+                            ok = false;
+                            break;
+                        }
+                        const ulonglong2 *sg = stage + (int64_t)slot * CHU;
+                        ulonglong2 x[UPT];
+#pragma unroll
+                        for (int q = 0; q < UPT; q++) {
+                            const int64_t w = t + q * NCT;
+                            x[q] = (w < nun) ? sg[w] : make_ulonglong2(0, 0);
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty_bar[slot]);
+#pragma unroll
+                        for (int q = 0; q < UPT; q++) {
+                            if constexpr (Ls == 1) {
+                                Wide<Ld> a, b;
+                                wzero(a);
+                                wzero(b);
+                                a.w[0] = x[q].x;
+                                b.w[0] = x[q].y;
+                                wadd(acc[q][0], a);
+                                wadd(acc[q][VPU - 1], b);
+                            } else {
+                                Wide<Ld> a;
+                                wzero(a);
+                                a.w[0] = x[q].x;
+                                if constexpr (Ld >= 2) a.w[1] = x[q].y;
+                                wadd(acc[q][0], a);
+                            }
+                        }
+                        if (++slot == NS) {
+                            slot = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+#pragma unroll
+                    for (int q = 0; q < UPT; q++) {
+                        const int64_t w = t + q * NCT;
+                        if (w < nun)
+#pragma unroll
+                            for (int h = 0; h < VPU; h++) wstore(dst + ((cu0 + w) * VPU + h) * Ld, acc[q][h]);
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) abort_flag = 1;
+    }
+    __syncthreads();
+}
+
+// Vectorised warp gather for rows stored with 1 or 2 limbs: the row is a run of
+// 16-byte units (two 1-limb values or one 2-limb value); lane `lane` owns units
+// base + lane + 32 q (q < UPT), and NB neighbours' units are loaded before any
+// is added, so NB * UPT 16-byte loads per lane are in flight.
+template <int Ls, int Ld, int UPT, int NB>
+__device__ __forceinline__ void gather_row_vec(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                               const uint64_t *__restrict__ X, int64_t R,
+                                               uint64_t *__restrict__ out_row, int lane)
+{
+    static_assert(Ls == 1 || Ls == 2, "16-byte units hold whole values only for 1 or 2 limbs");
+    constexpr int VPU = 2 / Ls;  // values per unit
+    const int64_t units = R * Ls / 2;
+    const ulonglong2 *__restrict__ Xv = reinterpret_cast<const ulonglong2 *>(X);
+    for (int64_t base = 0; base < units; base += 32 * UPT) {
+        Wide<Ld> acc[UPT][VPU];
+#pragma unroll
+        for (int q = 0; q < UPT; q++)
+#pragma unroll
+            for (int h = 0; h < VPU; h++) wzero(acc[q][h]);
+        for (int64_t e = e0; e < e1; e += 32) {
+            const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+            const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+            for (int t = 0; t < cnt; t += NB) {
+                ulonglong2 x[NB][UPT];
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    const int64_t u = __shfl_sync(0xffffffffu, myu, t + j < cnt ? t + j : t);
+                    const ulonglong2 *row = Xv + u * units;
+#pragma unroll
+                    for (int q = 0; q < UPT; q++) {
+                        const int64_t w = base + q * 32 + lane;
+                        x[j][q] = (w < units && t + j < cnt) ? __ldg(row + w) : make_ulonglong2(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    if (t + j >= cnt) break;
+#pragma unroll
+                    for (int q = 0; q < UPT; q++) {
+                        if constexpr (Ls == 1) {
+                            Wide<Ld> a, b;
+                            wzero(a);
+                            wzero(b);
+                            a.w[0] = x[j][q].x;
+                            b.w[0] = x[j][q].y;
+                            wadd(acc[q][0], a);
+                            wadd(acc[q][VPU - 1], b);
+                        } else {
+                            Wide<Ld> a;
+                            wzero(a);
+                            a.w[0] = x[j][q].x;
+                            if constexpr (Ld >= 2) a.w[1] = x[j][q].y;
+                            wadd(acc[q][0], a);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UPT; q++) {
+            const int64_t w = base + q * 32 + lane;
+            if (w < units)
+#pragma unroll
+                for (int h = 0; h < VPU; h++) wstore(out_row + (w * VPU + h) * Ld, acc[q][h]);
+        }
+    }
+}
+
+template <int Ls, int Ld, int UPT, int NB>
+__global__ void __launch_bounds__(kWarps * 32)
+gather_light_vec_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
+                        const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
+                        uint64_t *__restrict__ agg)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t v = v0 + blockIdx.x * (int64_t)kWarps + warp;
+    if (v >= v1) return;
+    const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+    if (e1 - e0 > split) return;  // heavy vertex: handled by tasks
+    gather_row_vec<Ls, Ld, UPT, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+}
+
+template <int Ls, int Ld, int UPT, int NB>
+__global__ void __launch_bounds__(kWarps * 32)
+gather_tasks_vec_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
+                        const int64_t *__restrict__ task_e, const uint64_t *__restrict__ X, int64_t R,
+                        uint64_t *__restrict__ partial)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = t0 + blockIdx.x * (int64_t)kWarps + warp;
+    if (t >= t1) return;
+    gather_row_vec<Ls, Ld, UPT, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
+                                    lane);
+}
+
+// Group gather: a group of G threads (G = 32..256, a whole number of warps)
+// covers a row's 16-byte units in one pass (thread gt owns units gt + G q,
+// q < UPT), so even a vertex with one neighbour has its whole row in flight;
+// NB neighbours are loaded before adding.  Each warp of the group fetches the
+// neighbour ids itself (32 per load) and broadcasts them with shuffles.
+template <int Ls, int Ld, int UPT, int NB>
+__global__ void __launch_bounds__(256)
+gather_group_kernel(int64_t a, int64_t b, int G, int tasks, int64_t split, const int64_t *__restrict__ row_ptr,
+                    const int64_t *__restrict__ task_e, const int32_t *__restrict__ col_idx,
+                    const uint64_t *__restrict__ X, int64_t R, uint64_t *__restrict__ out)
+{
+    static_assert(Ls == 1 || Ls == 2, "16-byte units hold whole values only for 1 or 2 limbs");
+    constexpr int VPU = 2 / Ls;
+    const int gpc = blockDim.x / G;
+    const int grp = threadIdx.x / G, gt = threadIdx.x - grp * G, lane = threadIdx.x & 31;
+    const int64_t item = a + (int64_t)blockIdx.x * gpc + grp;
+    if (item >= b) return;  // whole groups (whole warps) leave together
+    int64_t e0, e1;
+    if (tasks) {
+        e0 = task_e[2 * item];
+        e1 = task_e[2 * item + 1];
+    } else {
+        e0 = row_ptr[item];
+        e1 = row_ptr[item + 1];
+        if (e1 - e0 > split) return;  // heavy vertex: handled by tasks
+    }
+    const int64_t units = R * Ls / 2;
+    const ulonglong2 *__restrict__ Xv = reinterpret_cast<const ulonglong2 *>(X);
+    uint64_t *out_row = out + (item - a) * R * Ld;
+    for (int64_t base = 0; base < units; base += (int64_t)G * UPT) {
+        Wide<Ld> acc[UPT][VPU];
+#pragma unroll
+        for (int q = 0; q < UPT; q++)
+#pragma unroll
+            for (int h = 0; h < VPU; h++) wzero(acc[q][h]);
+        for (int64_t e = e0; e < e1; e += 32) {
+            const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+            const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+            // one warp of the group requests the batch's rows into L2 whole
+            if (base == 0 && gt < 32 && lane < cnt) prefetch_l2(Xv + (int64_t)myu * units, (uint32_t)(units * 16));
+            for (int t = 0; t < cnt; t += NB) {
+                ulonglong2 x[NB][UPT];
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    const int64_t u = __shfl_sync(0xffffffffu, myu, t + j < cnt ? t + j : t);
+                    const ulonglong2 *row = Xv + u * units;
+#pragma unroll
+                    for (int q = 0; q < UPT; q++) {
+                        const int64_t w = base + gt + (int64_t)q * G;
+                        x[j][q] = (w < units && t + j < cnt) ? __ldg(row + w) : make_ulonglong2(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+#pragma unroll
+                    for (int q = 0; q < UPT; q++) {
+                        if constexpr (Ls == 1) {
+                            Wide<Ld> lo, hi;
+                            wzero(lo);
+                            wzero(hi);
+                            lo.w[0] = x[j][q].x;
+                            hi.w[0] = x[j][q].y;
+                            wadd(acc[q][0], lo);
+                            wadd(acc[q][VPU - 1], hi);
+                        } else {
+                            Wide<Ld> v;
+                            wzero(v);
+                            v.w[0] = x[j][q].x;
+                            if constexpr (Ld >= 2) v.w[1] = x[j][q].y;
+                            wadd(acc[q][0], v);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UPT; q++) {
+            const int64_t w = base + gt + (int64_t)q * G;
+            if (w < units)
+#pragma unroll
+                for (int h = 0; h < VPU; h++) wstore(out_row + (w * VPU + h) * Ld, acc[q][h]);
+        }
+    }
+}
+
+template <int Ls, int Ld, int VPT, bool PF = false>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
@@ -137,10 +606,10 @@ gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__rest
     if (v >= v1) return;
     const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
     if (e1 - e0 > split) return;  // heavy vertex: handled by tasks
-    gather_row<Ls, Ld, VPT>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+    gather_row<Ls, Ld, VPT, PF>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
 }
 
-template <int Ls, int Ld, int VPT>
+template <int Ls, int Ld, int VPT, bool PF = false>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
                     const int64_t *__restrict__ task_e, const uint64_t *__restrict__ X, int64_t R,
@@ -149,8 +618,8 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = t0 + blockIdx.x * (int64_t)kWarps + warp;
     if (t >= t1) return;
-    gather_row<Ls, Ld, VPT>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
-                            lane);
+    gather_row<Ls, Ld, VPT, PF>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
+                                lane);
 }
 
 template <int Ld>
@@ -173,68 +642,80 @@ gather_reduce_kernel(int64_t h0, int64_t h1, int64_t v0, int64_t t0, const int32
     }
 }
 
+// Rows carry Cs >= C columns (C rounded up to even so a row is a whole number of
+// 16-byte units); columns C..Cs-1 are written as zero.
 template <int L>
-__global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Ca, int64_t Cp, int64_t npairs,
-                                       const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
-                                       const uint64_t *__restrict__ agg, uint64_t *__restrict__ out)
+__global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps,
+                                       int64_t npairs, const uint32_t *__restrict__ pairs,
+                                       const uint64_t *__restrict__ act, const uint64_t *__restrict__ agg,
+                                       uint64_t *__restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vb = i / Ch, s = i - vb * Ch;
-        const uint64_t *ar = act + vb * Ca * L;
-        const uint64_t *pr = agg + vb * Cp * L;
+        const int64_t vb = i / Chs, s = i - vb * Chs;
         Wide<L> acc;
         wzero(acc);
-        for (int64_t q = 0; q < npairs; q++) {
-            const uint32_t pq = __ldg(pairs + q * Ch + s);
-            wmac(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), wload<L, L>(pr + (pq >> 16) * L));
+        if (s < Ch) {
+            const uint64_t *ar = act + vb * Cas * L;
+            const uint64_t *pr = agg + vb * Cps * L;
+            for (int64_t q = 0; q < npairs; q++) {
+                const uint32_t pq = __ldg(pairs + q * Ch + s);
+                wmac(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), wload<L, L>(pr + (pq >> 16) * L));
+            }
         }
         wstore(out + i * L, acc);
     }
 }
 
 template <int L, bool HIST>
-__global__ void combine_select_kernel(int64_t total, int64_t v0, int B, int k, int64_t Ch, int64_t Cp,
+__global__ void combine_select_kernel(int64_t total, int64_t v0, int B, int k, int64_t Ch, int64_t Chs, int64_t Cps,
                                       const uint16_t *__restrict__ rm, const uint8_t *__restrict__ col,
                                       const void *__restrict__ aggp, uint64_t *__restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vb = i / Ch, s = i - vb * Ch;
-        const int64_t lv = vb / B;
-        const int b = (int)(vb - lv * B);
-        const int c = col[(v0 + lv) * B + b];
-        const uint32_t r = rm[s * k + c];
+        const int64_t vb = i / Chs, s = i - vb * Chs;
         Wide<L> x;
         wzero(x);
-        if (r != 0xFFFFu) {
-            if constexpr (HIST) {
-                x.w[0] = reinterpret_cast<const uint32_t *>(aggp)[vb * k + r];
-            } else {
-                x = wload<L, L>(reinterpret_cast<const uint64_t *>(aggp) + (vb * Cp + r) * L);
+        if (s < Ch) {
+            const int64_t lv = vb / B;
+            const int b = (int)(vb - lv * B);
+            const int c = col[(v0 + lv) * B + b];
+            const uint32_t r = rm[s * k + c];
+            if (r != 0xFFFFu) {
+                if constexpr (HIST) {
+                    x.w[0] = reinterpret_cast<const uint32_t *>(aggp)[vb * k + r];
+                } else {
+                    x = wload<L, L>(reinterpret_cast<const uint64_t *>(aggp) + (vb * Cps + r) * L);
+                }
             }
         }
         wstore(out + i * L, x);
     }
 }
 
+// p = 1: out[S] = sum over c in S of act[S \ {c}] * hist[c].  The h members of S
+// come from the (h, h-1) split table: entry q of S is rank(S \ {c}) | c << 16
+// (the colex rank of {c} is c), laid out [q][S] so a warp reads it coalesced.
 template <int L>
-__global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Ca,
-                                    const uint16_t *__restrict__ rm, const uint64_t *__restrict__ act,
+__global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Chs, int64_t Cas, int h,
+                                    const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
                                     const uint32_t *__restrict__ hist, uint64_t *__restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vb = i / Ch, s = i - vb * Ch;
-        const uint64_t *ar = act + vb * Ca * L;
-        const uint32_t *hr = hist + vb * k;
+        const int64_t vb = i / Chs, s = i - vb * Chs;
         Wide<L> acc;
         wzero(acc);
-        for (int c = 0; c < k; c++) {
-            const uint32_t r = rm[s * k + c];
-            if (r == 0xFFFFu) continue;
-            const uint32_t hc = hr[c];
-            if (hc) wmac_small(acc, wload<L, L>(ar + r * L), hc);
+        if (s < Ch) {
+            const uint64_t *ar = act + vb * Cas * L;
+            const uint32_t *hr = hist + vb * k;
+#pragma unroll 4
+            for (int q = 0; q < h; q++) {
+                const uint32_t pq = __ldg(pairs + q * Ch + s);
+                const uint32_t hc = hr[pq >> 16];
+                if (hc) wmac_small(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), hc);
+            }
         }
         wstore(out + i * L, acc);
     }
@@ -366,21 +847,29 @@ inline unsigned grid_stride_ctas(int64_t items, int threads)
 }
 
 template <int Ls, int Ld>
-void gather_light_t(cudaStream_t st, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
+void gather_light_t(cudaStream_t st, bool pf, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                     const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    gather_light_kernel<Ls, Ld, VPT><<<grid_for(v1 - v0, kWarps), kWarps * 32, 0, st>>>(v0, v1, split, rp, ci,
-                                                                                         X, R, agg);
+    if (pf)
+        gather_light_kernel<Ls, Ld, VPT, true><<<grid_for(v1 - v0, kWarps), kWarps * 32, 0, st>>>(v0, v1, split, rp,
+                                                                                               ci, X, R, agg);
+    else
+        gather_light_kernel<Ls, Ld, VPT, false><<<grid_for(v1 - v0, kWarps), kWarps * 32, 0, st>>>(v0, v1, split, rp,
+                                                                                                ci, X, R, agg);
 }
 
 template <int Ls, int Ld>
-void gather_tasks_t(cudaStream_t st, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
+void gather_tasks_t(cudaStream_t st, bool pf, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
                     const uint64_t *X, int64_t R, uint64_t *partial)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    gather_tasks_kernel<Ls, Ld, VPT><<<grid_for(t1 - t0, kWarps), kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R,
-                                                                                         partial);
+    if (pf)
+        gather_tasks_kernel<Ls, Ld, VPT, true><<<grid_for(t1 - t0, kWarps), kWarps * 32, 0, st>>>(t0, t1, ci, te, X,
+                                                                                               R, partial);
+    else
+        gather_tasks_kernel<Ls, Ld, VPT, false><<<grid_for(t1 - t0, kWarps), kWarps * 32, 0, st>>>(t0, t1, ci, te, X,
+                                                                                                R, partial);
 }
 
 #define CC_DISPATCH_L(L, ...)                  \
@@ -410,10 +899,10 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
-                         uint64_t *agg)
+                         uint64_t *agg, bool prefetch)
 {
     if (v1 <= v0) return;
-#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, v0, v1, split, row_ptr, col_idx, X, R, agg)
+#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, v0, v1, split, row_ptr, col_idx, X, R, agg)
     CC_GL(1, 1); CC_GL(1, 2); CC_GL(1, 3); CC_GL(1, 4);
     CC_GL(2, 1); CC_GL(2, 2); CC_GL(2, 3); CC_GL(2, 4);
     CC_GL(3, 1); CC_GL(3, 2); CC_GL(3, 3); CC_GL(3, 4);
@@ -421,11 +910,164 @@ void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1
 #undef CC_GL
 }
 
-void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
-                         const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial)
+namespace {
+
+template <int Ls, int Ld>
+void gather_bulk_t(cudaStream_t st, const BulkItems &it, const int32_t *ci, const uint64_t *X, int64_t R,
+                   uint64_t *out, int *err)
+{
+    constexpr int UPT = 2;
+    const int64_t stage_bytes = std::min<int64_t>((int64_t)kBulkConsumers * 32 * UPT, R * Ls / 2) * 16;
+    const int NS = (int)std::max<int64_t>(2, std::min<int64_t>(kBulkMaxStages, kBulkSmemBytes / stage_bytes));
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    gather_bulk_kernel<Ls, Ld, UPT><<<sms, kBulkThreads, (size_t)NS * stage_bytes, st>>>(it, ci, X, R, out, NS, err);
+}
+
+void gather_bulk_dispatch(cudaStream_t st, int Ls, int Ld, const BulkItems &it, const int32_t *ci,
+                          const uint64_t *X, int64_t R, uint64_t *out, int *err)
+{
+#define CC_GB(a, b) if (Ls == a && Ld == b) return gather_bulk_t<a, b>(st, it, ci, X, R, out, err)
+    CC_GB(1, 1); CC_GB(1, 2); CC_GB(1, 3); CC_GB(1, 4);
+    CC_GB(2, 1); CC_GB(2, 2); CC_GB(2, 3); CC_GB(2, 4);
+#undef CC_GB
+}
+
+template <int Ls, int Ld>
+void gather_vec_t(cudaStream_t st, bool tasks, int64_t a, int64_t b, int64_t split, const int64_t *rp,
+                  const int32_t *ci, const int64_t *te, const uint64_t *X, int64_t R, uint64_t *out)
+{
+    constexpr int UPT = 4, NB = 4;
+    if (tasks)
+        gather_tasks_vec_kernel<Ls, Ld, UPT, NB><<<grid_for(b - a, kWarps), kWarps * 32, 0, st>>>(a, b, ci, te, X, R,
+                                                                                                  out);
+    else
+        gather_light_vec_kernel<Ls, Ld, UPT, NB><<<grid_for(b - a, kWarps), kWarps * 32, 0, st>>>(a, b, split, rp, ci,
+                                                                                                  X, R, out);
+}
+
+void gather_vec_dispatch(cudaStream_t st, bool tasks, int Ls, int Ld, int64_t a, int64_t b, int64_t split,
+                         const int64_t *rp, const int32_t *ci, const int64_t *te, const uint64_t *X, int64_t R,
+                         uint64_t *out)
+{
+#define CC_GV(x, y) if (Ls == x && Ld == y) return gather_vec_t<x, y>(st, tasks, a, b, split, rp, ci, te, X, R, out)
+    CC_GV(1, 1); CC_GV(1, 2); CC_GV(1, 3); CC_GV(1, 4);
+    CC_GV(2, 1); CC_GV(2, 2); CC_GV(2, 3); CC_GV(2, 4);
+#undef CC_GV
+}
+
+}  // namespace
+
+namespace {
+
+template <int Ls, int Ld>
+void gather_group_t(cudaStream_t st, bool tasks, int64_t a, int64_t b, int64_t split, const int64_t *rp,
+                    const int64_t *te, const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *out)
+{
+    constexpr int UPT = 4, NB = 2;
+    const int64_t units = R * Ls / 2;
+    int G = 32;
+    while (G < 256 && (int64_t)G * UPT < units) G <<= 1;
+    const int gpc = 256 / G;
+    gather_group_kernel<Ls, Ld, UPT, NB><<<grid_for(b - a, gpc), 256, 0, st>>>(a, b, G, tasks ? 1 : 0, split, rp, te,
+                                                                              ci, X, R, out);
+}
+
+void gather_group_dispatch(cudaStream_t st, bool tasks, int Ls, int Ld, int64_t a, int64_t b, int64_t split,
+                           const int64_t *rp, const int64_t *te, const int32_t *ci, const uint64_t *X, int64_t R,
+                           uint64_t *out)
+{
+#define CC_GG(x, y) if (Ls == x && Ld == y) return gather_group_t<x, y>(st, tasks, a, b, split, rp, te, ci, X, R, out)
+    CC_GG(1, 1); CC_GG(1, 2); CC_GG(1, 3); CC_GG(1, 4);
+    CC_GG(2, 1); CC_GG(2, 2); CC_GG(2, 3); CC_GG(2, 4);
+#undef CC_GG
+}
+
+}  // namespace
+
+void launch_gather_light_group(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                               const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
+                               uint64_t *agg)
+{
+    if (v1 <= v0) return;
+    gather_group_dispatch(st, false, Ls, Ld, v0, v1, split, row_ptr, nullptr, col_idx, X, R, agg);
+}
+
+void launch_gather_tasks_group(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                               const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial)
 {
     if (t1 <= t0) return;
-#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, t0, t1, col_idx, task_e, X, R, partial)
+    gather_group_dispatch(st, true, Ls, Ld, t0, t1, 0, nullptr, task_e, col_idx, X, R, partial);
+}
+
+bool vec_gather_ok(int Ls, int64_t R) { return (Ls == 1 || Ls == 2) && (R * Ls) % 2 == 0; }
+
+void launch_gather_light_vec(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                             const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
+                             uint64_t *agg)
+{
+    if (v1 <= v0) return;
+    gather_vec_dispatch(st, false, Ls, Ld, v0, v1, split, row_ptr, col_idx, nullptr, X, R, agg);
+}
+
+void launch_gather_tasks_vec(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                             const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial)
+{
+    if (t1 <= t0) return;
+    gather_vec_dispatch(st, true, Ls, Ld, t0, t1, 0, nullptr, col_idx, task_e, X, R, partial);
+}
+
+bool bulk_gather_ok(int Ls, int64_t R)
+{
+    // whole values per 16-byte unit, whole units per row, rows big enough to amortise a copy
+    return (Ls == 1 || Ls == 2) && (R * Ls) % 2 == 0 && R * Ls * 8 >= 1024;
+}
+
+void init_kernel_attributes()
+{
+#define CC_ATTR(a, b)                                                                                       \
+    cudaFuncSetAttribute(gather_bulk_kernel<a, b, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                         (int)kBulkSmemBytes)
+    CC_ATTR(1, 1); CC_ATTR(1, 2); CC_ATTR(1, 3); CC_ATTR(1, 4);
+    CC_ATTR(2, 1); CC_ATTR(2, 2); CC_ATTR(2, 3); CC_ATTR(2, 4);
+#undef CC_ATTR
+}
+
+void launch_gather_light_bulk(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                              const int64_t *row_ptr, const int32_t *col_idx, int64_t nnz, const uint64_t *X,
+                              int64_t R, uint64_t *agg, int *err)
+{
+    if (v1 <= v0) return;
+    BulkItems it{};
+    it.mode = 0;
+    it.nnz = nnz;
+    it.v0 = v0;
+    it.v1 = v1;
+    it.split = split;
+    it.row_ptr = row_ptr;
+    gather_bulk_dispatch(st, Ls, Ld, it, col_idx, X, R, agg, err);
+}
+
+void launch_gather_tasks_bulk(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                              int64_t nnz, const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial,
+                              int *err)
+{
+    if (t1 <= t0) return;
+    BulkItems it{};
+    it.mode = 1;
+    it.nnz = nnz;
+    it.t0 = t0;
+    it.t1 = t1;
+    it.task_e = task_e;
+    gather_bulk_dispatch(st, Ls, Ld, it, col_idx, X, R, partial, err);
+}
+
+void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                         const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial, bool prefetch)
+{
+    if (t1 <= t0) return;
+#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, t0, t1, col_idx, task_e, X, R, partial)
     CC_GT(1, 1); CC_GT(1, 2); CC_GT(1, 3); CC_GT(1, 4);
     CC_GT(2, 1); CC_GT(2, 2); CC_GT(2, 3); CC_GT(2, 4);
     CC_GT(3, 1); CC_GT(3, 2); CC_GT(3, 3); CC_GT(3, 4);
@@ -442,40 +1084,38 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
                           h0, h1, v0, t0, heavy_v, heavy_tptr, partial, R, agg));
 }
 
-void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Ca, int64_t Cp,
-                            int64_t npairs, const uint32_t *pairs, const uint64_t *act, const uint64_t *agg,
-                            uint64_t *out)
+void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Chs, int64_t Cas,
+                            int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
+                            const uint64_t *agg, uint64_t *out)
 {
-    const int64_t total = nv * B * Ch;
+    const int64_t total = nv * B * Chs;
     if (total == 0) return;
     CC_DISPATCH_L(L, combine_generic_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                         total, Ch, Ca, Cp, npairs, pairs, act, agg, out));
+                         total, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out));
 }
 
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
-                           int64_t Ch, int64_t Cp, const uint16_t *rm, const uint8_t *col, const void *agg,
-                           uint64_t *out)
+                           int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
+                           const void *agg, uint64_t *out)
 {
-    const int64_t total = nv * B * Ch;
+    const int64_t total = nv * B * Chs;
     if (total == 0) return;
     if (agg_is_hist) {
         CC_DISPATCH_L(L, combine_select_kernel<LL, true><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                             total, v0, B, k, Ch, Cp, rm, col, agg, out));
+                             total, v0, B, k, Ch, Chs, Cps, rm, col, agg, out));
     } else {
         CC_DISPATCH_L(L, combine_select_kernel<LL, false><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                             total, v0, B, k, Ch, Cp, rm, col, agg, out));
+                             total, v0, B, k, Ch, Chs, Cps, rm, col, agg, out));
     }
 }
 
-void launch_combine_hist(cudaStream_t st, int L, int64_t v0, int64_t nv, int B, int k, int64_t Ch, int64_t Ca,
-                         int h, const uint16_t *rm, const uint64_t *act, const uint32_t *hist, uint64_t *out)
+void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64_t Ch, int64_t Chs, int64_t Cas,
+                         int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist, uint64_t *out)
 {
-    (void)v0;
-    (void)h;
-    const int64_t total = nv * B * Ch;
+    const int64_t total = nv * B * Chs;
     if (total == 0) return;
     CC_DISPATCH_L(L, combine_hist_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                         total, k, Ch, Ca, rm, act, hist, out));
+                         total, k, Ch, Chs, Cas, h, pairs, act, hist, out));
 }
 
 int64_t reduce_scratch_ctas() { return 152 * 2; }

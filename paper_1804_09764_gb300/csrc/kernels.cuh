@@ -3,7 +3,8 @@
 // Data layout in device memory (one "pass" processes B colourings at once):
 //   colours  col[v * B + b]                       uint8
 //   hist     hist[(v * B + b) * k + c]            uint32  (leaf gather, p = 1)
-//   tables   X[((v * B + b) * C + s) * L + limb]  uint64  (C = C(k, |T|) colex columns)
+//   tables   X[((v * B + b) * Cs + s) * L + limb] uint64  (C(k, |T|) colex columns,
+//                                                         row stride Cs = col_stride(C))
 // v runs over the active (non-isolated) vertices in the library's compact
 // numbering.  A "block" is a contiguous vertex range [v0, v1) whose working
 // rows (aggregates, chain intermediates) are stored at local row v - v0.
@@ -28,32 +29,64 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 
 // agg[v - v0] = sum_{u in N(v)} X[u]  over rows of R values; light vertices only
 // (deg <= split), heavy ones go through tasks + reduce.
+// prefetch: also request each neighbour row whole into L2 (cp.async.bulk.prefetch)
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
-                         int64_t R, uint64_t *agg);
+                         int64_t R, uint64_t *agg, bool prefetch = false);
 
 // tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
                          const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
-                         int64_t R, uint64_t *partial);
+                         int64_t R, uint64_t *partial, bool prefetch = false);
+
+// Vectorised warp versions (16-byte loads, several neighbours in flight) for
+// rows of 1- or 2-limb values; usable when vec_gather_ok(Ls, R).
+bool vec_gather_ok(int Ls, int64_t R);
+void launch_gather_light_vec(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                             const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
+                             uint64_t *agg);
+void launch_gather_tasks_vec(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                             const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial);
+
+// Group versions: 32..256 threads per row so the whole row is loaded in one
+// pass (rows of 1- or 2-limb values; same condition as the vectorised kernels).
+void launch_gather_light_group(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                               const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
+                               uint64_t *agg);
+void launch_gather_tasks_group(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                               const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial);
+
+// Bulk-copy (TMA) versions of the two gathers above: persistent CTAs stream
+// neighbour-row segments into shared memory through an mbarrier ring.  Usable
+// when bulk_gather_ok(Ls, R).  *err receives a non-zero code if a wait timed out.
+bool bulk_gather_ok(int Ls, int64_t R);
+// once per process and device before the first launch (shared-memory opt-in)
+void init_kernel_attributes();
+void launch_gather_light_bulk(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                              const int64_t *row_ptr, const int32_t *col_idx, int64_t nnz, const uint64_t *X,
+                              int64_t R, uint64_t *agg, int *err);
+void launch_gather_tasks_bulk(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
+                              int64_t nnz, const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial,
+                              int *err);
 
 // heavy vertices [h0, h1) of the heavy list: agg[v - v0] = sum of their partial rows
 void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64_t v0, int64_t t0,
                           const int32_t *heavy_v, const int64_t *heavy_tptr, const uint64_t *partial,
                           int64_t R, uint64_t *agg);
 
-// combine kernels (Eq. 1 inner sum).  Rows: act C(k,a), agg C(k,p), out C(k,h); B per vertex.
-void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Ca,
-                            int64_t Cp, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
+// combine kernels (Eq. 1 inner sum).  Rows: act C(k,a), agg C(k,p), out C(k,h)
+// valid columns, stored with strides Cas, Cps, Chs (>= the column counts; extra
+// output columns are written as zero); B rows per vertex.
+void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Chs, int64_t Cas,
+                            int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
                             const uint64_t *agg, uint64_t *out);
 // a = 1: act is the single vertex v with colour col(v)
-void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B,
-                           int k, int64_t Ch, int64_t Cp, const uint16_t *rm, const uint8_t *col,
+void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
+                           int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
                            const void *agg, uint64_t *out);
-// p = 1: agg is the colour histogram of N(v)
-void launch_combine_hist(cudaStream_t st, int L, int64_t v0, int64_t nv, int B, int k, int64_t Ch,
-                         int64_t Ca, int h, const uint16_t *rm, const uint64_t *act,
-                         const uint32_t *hist, uint64_t *out);
+// p = 1: agg is the colour histogram of N(v); pairs = the (h, h-1) split table
+void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64_t Ch, int64_t Chs, int64_t Cas,
+                         int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist, uint64_t *out);
 
 // totals[b] += sum_v root[v][b]  (root rows hold C(k,k) = 1 column)
 void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_t *root,
@@ -74,5 +107,9 @@ void launch_max_sum(cudaStream_t st, int64_t n, const double *x, double *out);
 void launch_remap(cudaStream_t st, int64_t nnz, const int32_t *src, const int32_t *new_id, int32_t *dst);
 
 int64_t reduce_scratch_ctas();
+
+// Row stride (in values) of a table with C colour-set columns: C rounded up to
+// even, so every row and row segment is a whole number of 16-byte units.
+inline int64_t col_stride(int64_t C) { return (C + 1) & ~int64_t(1); }
 
 }  // namespace cc

@@ -110,10 +110,16 @@ struct PlanInstance {
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;
     uint64_t off_col = 0, off_hist = 0, off_act[2] = {0, 0}, off_agg = 0, off_partial = 0, off_root = 0,
-             off_scratch = 0, off_totals = 0, off_params = 0;
+             off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0;
     std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
     // analytic figures
     double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0;
+    // autotuner: gather kernel variant per gather site (chain, step), chosen by
+    // timing every applicable variant on the first pass
+    std::map<std::pair<int, int>, int> site_mode;
+    bool tuned = false;
+    struct Trial { int chain, step, mode; cudaEvent_t a, b; };
+    std::vector<Trial> trials;
 };
 
 enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_SELECT, K_CHIST, K_KINDS };
@@ -131,6 +137,17 @@ struct KernelTimer {
 
 struct Request;
 
+// A plan kept between cc_count calls with its workspace and, when enabled, the
+// per-pass schedule captured as a CUDA graph (pointers into the workspace are
+// fixed, so the graph can be replayed with new colouring parameters).
+struct CachedPlan {
+    std::unique_ptr<PlanInstance> p;
+    char *ws = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches_per_pass = 0;
+    uint64_t last_use = 0;
+};
+
 struct Ctx {
     cc_options opt;
     int device = 0;
@@ -145,6 +162,11 @@ struct Ctx {
     std::map<int64_t, std::unique_ptr<Template>> templates;
     KernelTimer timer;
     std::atomic<int64_t> launches{0};
+    // plans kept between calls: (graph, template, batch cap, width) -> plan
+    std::map<std::tuple<int64_t, int64_t, int, int>, CachedPlan> plan_cache;
+    uint64_t use_clock = 0;
+    // autotuned gather variants per (graph, template, batch), shared by later plans
+    std::map<std::tuple<int64_t, int64_t, int>, std::map<std::pair<int, int>, int>> tuned_modes;
     // serving
     std::unique_ptr<struct Server> server;
     Ctx();
@@ -176,7 +198,8 @@ void free_plan(Ctx *c, PlanInstance *p);
 // copied to host_totals / host_samples (pinned) at pass offsets.
 cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int pass0, int pass1,
                      cudaStream_t st, ColourParams *host_params, uint64_t *host_totals, uint64_t *host_samples,
-                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out);
+                     const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out,
+                     CachedPlan *graph = nullptr);
 
 // Host post-processing: copies, estimate, median of means, writes caller buffers.
 cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
@@ -185,6 +208,11 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
 
 cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
                      uint64_t *maps, uint64_t *sample_out, cc_result *res);
+
+// drop cached plans (all, or those of one graph / template); frees their workspace
+void evict_plans(Ctx *c, int64_t gid = -1, int64_t tid = -1);
+// arena allocation that drops cached plans and retries once when the arena is full
+void *arena_alloc(Ctx *c, uint64_t bytes);
 
 // serving (serve.cpp)
 cc_status serve_submit(Ctx *c, const cc_request *r, cc_req_id *out);

@@ -139,6 +139,10 @@ bool admit(Ctx *c, Server *s, Request *r)
     }
     std::unique_ptr<PlanInstance> p;
     cc_status rc = make_plan(c, r->req.graph, r->req.tmpl, r->job.n_iter, c->opt.width_bits, stream, &p);
+    if (rc == CC_ERR_BUDGET && !c->plan_cache.empty()) {
+        evict_plans(c);  // plans cached by cc_count give way to served requests
+        rc = make_plan(c, r->req.graph, r->req.tmpl, r->job.n_iter, c->opt.width_bits, stream, &p);
+    }
     if (rc == CC_ERR_BUDGET && !s->active.empty()) {
         git->second->in_use--;
         s->streams.push_back(stream);
@@ -149,7 +153,7 @@ bool admit(Ctx *c, Server *s, Request *r)
         complete(c, s, r, rc, cc_last_error());
         return true;
     }
-    r->ws = (char *)c->arena.alloc(p->ws_bytes);
+    r->ws = (char *)arena_alloc(c, p->ws_bytes);
     if (!r->ws) {
         free_plan(c, p.get());
         if (!s->active.empty()) {
@@ -163,12 +167,18 @@ bool admit(Ctx *c, Server *s, Request *r)
         return true;
     }
     r->plan = std::move(p);
+    r->plan->tuned = true;  // served passes use the tuned variants if a count tuned them, else the defaults
     r->npass = (r->job.n_iter + r->plan->B - 1) / r->plan->B;
     if (cudaMallocHost(&r->hp, sizeof(ColourParams) * r->npass) != cudaSuccess ||
         cudaMallocHost(&r->ht, (size_t)8 * r->npass * r->plan->B * r->plan->L_root) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         complete(c, s, r, CC_ERR_CUDA, "pinned buffer or event creation failed");
+        return true;
+    }
+    if (cudaMemsetAsync(r->ws + r->plan->off_err, 0, 256, stream) != cudaSuccess) {
+        cudaGetLastError();
+        complete(c, s, r, CC_ERR_CUDA, "workspace clear failed");
         return true;
     }
     r->state = Request::RUNNING;
@@ -246,6 +256,14 @@ void worker(Server *s)
                     continue;
                 }
                 // all passes finished
+                int kerr = 0;
+                if (cudaMemcpy(&kerr, r->ws + r->plan->off_err, sizeof kerr, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                    kerr) {
+                    s->active.erase(s->active.begin() + i);
+                    complete(c, s, r, CC_ERR_TIMEOUT, "a gather kernel wait ran out of time");
+                    progress = true;
+                    continue;
+                }
                 Graph *g = c->graphs.at(r->req.graph).get();
                 int L = r->plan->L_root;
                 r->counts.assign((size_t)r->job.n_iter * L, 0);

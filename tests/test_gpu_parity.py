@@ -251,3 +251,45 @@ def test_table_gather_matches_oracle_neighbour_sum(limbs, split):
     c.table_gather(rp, ci, Xt, A, values, limbs, split)
     assert np.array_equal(A.cpu().numpy().view(np.uint64), expect)
     c.close()
+
+
+def test_bulk_and_warp_gathers_agree_with_oracle():
+    # gather_mode 0: bulk-copy (TMA) gather for rows of >= 1 KiB; 1: scalar warp
+    # gather; 2: vectorised warp gather; 3: group gather; 4: warp gather + L2 prefetch
+    g = gg.rmat_graph(11, seed=21)
+    k, e = gg.template_edges("tree12")
+    maps = oracle_maps(g, k, e, 1, 13, range(3))
+    for mode in (0, 1, 2, 3, 4):
+        c = make_ctx(gather_mode=mode, split_threshold=12, batch=2, block_vertices=900)
+        gid = c.graph_load(g)
+        tid = c.template_load(k, e, 1)
+        res = c.count(gid, tid, seed=13, n_iter=3, want_maps=True)
+        assert res["maps"] == maps, f"gather_mode {mode}"
+        c.close()
+
+
+def test_cuda_graph_replay_and_plan_cache():
+    # the per-pass schedule captured once as a CUDA graph and replayed for every
+    # pass and every later call with the same plan
+    g = gg.rmat_graph(10, seed=12)
+    k, e = gg.template_edges("caterpillar10")
+    c = make_ctx(use_cuda_graph=1, batch=2, split_threshold=16)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 2)
+    for first in (0, 5):
+        res = c.count(gid, tid, seed=21, n_iter=3, first_iter=first, want_maps=True)
+        assert res["maps"] == oracle_maps(g, k, e, 2, 21, range(first, first + 3))
+    c.close()
+
+
+def test_autotuned_plan_matches_oracle():
+    # the first pass times every gather variant per site; all passes must stay exact
+    g = gg.rmat_graph(11, seed=33)
+    k, e = gg.template_edges("tree12")
+    c = make_ctx(autotune=1, use_cuda_graph=1, batch=2, split_threshold=40)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 1)
+    for first in (0, 4):
+        res = c.count(gid, tid, seed=5, n_iter=4, first_iter=first, want_maps=True)
+        assert res["maps"] == oracle_maps(g, k, e, 1, 5, range(first, first + 4))
+    c.close()

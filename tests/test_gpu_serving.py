@@ -1,0 +1,84 @@
+"""Continuous-batching serving loop: results in the mix equal results alone.
+
+Requests over several resident graphs and templates are submitted while others
+are running; every result must be bit-identical to the same count run alone
+through cc_count (exact integers: the tolerance is zero) and, for a sample, to
+the oracle.  Also: cancellation, unknown handles, and the latency statistics.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_09764_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+def make_ctx(**kw):
+    from paper_1804_09764_gb300 import cc
+
+    return cc.Context(budget_bytes=kw.pop("budget_bytes", 6 << 30), **kw)
+
+
+def test_mix_equals_alone():
+    rng = np.random.default_rng(42)
+    graphs = [gg.rmat_graph(10, seed=1), gg.rmat_graph(11, seed=2), gg.er_graph(3000, 8, seed=3)]
+    c = make_ctx(max_slots=3, batch=4)
+    gids = [c.graph_load(g) for g in graphs]
+    reqs = []
+    for i in range(14):
+        k = int(rng.integers(3, 10))
+        e = gg.prufer_tree(k, 500 + i)
+        gi = int(rng.integers(0, len(graphs)))
+        reqs.append(dict(g=gi, k=k, e=e, tid=c.template_load(k, e), seed=int(rng.integers(0, 2 ** 40)),
+                         n_iter=int(rng.integers(1, 7)), first=int(rng.integers(0, 100))))
+    # alone
+    for r in reqs:
+        r["alone"] = c.count(gids[r["g"]], r["tid"], seed=r["seed"], n_iter=r["n_iter"], first_iter=r["first"])
+    # in the mix: half up front, the rest while the first ones run
+    ids = []
+    for r in reqs[:7]:
+        ids.append(c.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"], r["first"]))
+    time.sleep(0.01)
+    for r in reqs[7:]:
+        ids.append(c.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"], r["first"]))
+    for rid, r in zip(ids, reqs):
+        res = c.wait(rid, r["n_iter"], timeout_s=120)
+        assert res["counts"] == r["alone"]["counts"]
+        assert res["estimate"] == r["alone"]["estimate"]
+    st = c.serve_stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert 0 < st["p50_latency_s"] <= st["p99_latency_s"]
+    # oracle spot check of two requests
+    for r in reqs[:2]:
+        g = graphs[r["g"]]
+        aut = O.automorphisms(r["k"], r["e"])
+        want = [O.count_maps(g, r["k"], r["e"], 0, seed=r["seed"], j=r["first"] + j) // aut
+                for j in range(r["n_iter"])]
+        assert r["alone"]["counts"] == want
+    c.close()
+
+
+def test_cancel_and_errors():
+    from paper_1804_09764_gb300 import cc
+
+    c = make_ctx(max_slots=1)
+    gid = c.graph_load(gg.rmat_graph(12, seed=7))
+    tid = c.template_load(*gg.template_edges("tree12"))
+    r1 = c.submit(gid, tid, 1, 8)
+    r2 = c.submit(gid, tid, 2, 8)   # queued behind r1 (one slot)
+    c.cancel(r2)
+    with pytest.raises(cc.CCError) as ei:
+        c.wait(r2, 8, timeout_s=120)
+    assert ei.value.status == -9
+    res = c.wait(r1, 8, timeout_s=120)
+    assert len(res["counts"]) == 8
+    with pytest.raises(cc.CCError) as ei:
+        c.poll(12345, 1)
+    assert ei.value.status == -10
+    with pytest.raises(cc.CCError) as ei:
+        c.submit(gid, 999, 1, 1)
+    assert ei.value.status == -10
+    c.close()
