@@ -299,8 +299,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=1,
-                    help="1 warp gather (default), 0 bulk-copy (TMA) ring, 2 warp 16-byte vectors, 3 group, "
-                         "4 warp + L2 prefetch")
+                    help="1 persistent warp gather (default), 5 one-pass warp gather, 0 bulk-copy (TMA) ring, "
+                         "2 warp 16-byte vectors, 3 group, 4 persistent warp + L2 prefetch")
     ap.add_argument("--budget-gb", type=float, default=0, help="HBM arena size (0: the workload's)")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
     ap.add_argument("--requests", type=int, default=200)
@@ -424,8 +424,9 @@ def main():
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
                    "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3),
-                   "gather": {0: "bulk-copy (TMA)", 1: "warp per row", 2: "warp (16-byte vectors)",
-                              3: "group (row per 32-256 threads)", 4: "warp + L2 prefetch"}[args.gather_mode]},
+                   "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row", 2: "warp (16-byte vectors)",
+                              3: "group (row per 32-256 threads)", 4: "persistent warp + L2 prefetch",
+                              5: "warp per row, one pass"}[args.gather_mode]},
         "hbm_frac_step": info["algorithmic_bytes_per_colouring"] * n_iter * args.steps / elapsed / 1e9 / peak,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),

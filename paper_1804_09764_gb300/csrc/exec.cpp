@@ -21,6 +21,7 @@ uint64_t splitmix64_host(uint64_t state)
 namespace {
 
 constexpr uint64_t kAl = 256;
+constexpr int kWorkCounters = 4096;  // per-pass work counters of the persistent gathers
 inline uint64_t rup(uint64_t x) { return (x + kAl - 1) / kAl * kAl; }
 
 int bits_for(double v)
@@ -85,7 +86,7 @@ int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(
 struct Layout {
     uint64_t bytes = 0;
     uint64_t off_col, off_hist, off_act[2], off_agg, off_partial, off_root, off_scratch, off_totals, off_params,
-        off_err;
+        off_err, off_ctr;
     std::vector<uint64_t> off_table;
     int64_t max_tasks = 0;
     std::vector<std::pair<int64_t, int64_t>> blocks;
@@ -165,6 +166,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     Lo.off_totals = take((uint64_t)B * 8 * p.L_root);
     Lo.off_params = take(sizeof(ColourParams));
     Lo.off_err = take(256);
+    Lo.off_ctr = take(kWorkCounters * 8);
     Lo.bytes = cur;
     return Lo;
 }
@@ -263,6 +265,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     p->off_totals = Lo.off_totals;
     p->off_params = Lo.off_params;
     p->off_err = Lo.off_err;
+    p->off_ctr = Lo.off_ctr;
     p->off_table = Lo.off_table;
     p->blocks = Lo.blocks;
     p->heavy = Lo.heavy;
@@ -403,6 +406,10 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     uint64_t *totals = (uint64_t *)W(p->off_totals);
     CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)B * 8 * p->L_root, st));
     uint8_t *col = (uint8_t *)W(p->off_col);
+    unsigned long long *ctr = (unsigned long long *)W(p->off_ctr);
+    int ctr_used = 0;
+    auto next_counter = [&]() -> unsigned long long * { return ctr_used < kWorkCounters ? ctr + ctr_used++ : nullptr; };
+    CC_CUDA(cudaMemsetAsync(ctr, 0, (size_t)kWorkCounters * 8, st));
     Ln.begin(K_COLOUR);
     launch_colour(st, g->n_act, B, k, g->orig, (const ColourParams *)W(p->off_params), col);
     Ln.end(1, (double)g->n_act * (8 + B));
@@ -474,7 +481,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 launch_gather_light_vec(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
                             else
                                 launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
-                                                    gm == 4);
+                                                    gm == 4, gm == 5 ? nullptr : next_counter());
                             int n = 1;
                             if (hv.t1 > hv.t0) {
                                 uint64_t *part = (uint64_t *)W(p->off_partial);
@@ -488,7 +495,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                     launch_gather_tasks_vec(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
                                 else
                                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
-                                                        gm == 4);
+                                                        gm == 4, gm == 5 ? nullptr : next_counter());
                                 launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
                                 n += 2;
@@ -499,7 +506,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         const auto site = std::make_pair((int)ci, (int)si);
                         if (tune) {
                             // every variant computes the same sums; the last one run leaves agg
-                            for (int gm : {0, 2, 3, 4, 1}) {  // the default (1) last
+                            for (int gm : {0, 2, 3, 4, 5, 1}) {  // the default (1) last
                                 if ((gm == 0 && !bulk_gather_ok(Ls, R)) || ((gm == 2 || gm == 3) && !vec_gather_ok(Ls, R)))
                                     continue;
                                 PlanInstance::Trial tr{(int)ci, (int)si, gm, nullptr, nullptr};

@@ -14,6 +14,8 @@
 #include "wideint.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 namespace cc {
 
@@ -595,31 +597,51 @@ gather_group_kernel(int64_t a, int64_t b, int G, int tasks, int64_t split, const
     }
 }
 
+// Warp per row.  With `next` == nullptr warp w of the grid takes item w (one
+// pass); otherwise the grid is persistent and each warp pulls its next item
+// from the counter, so a warp that finishes a short neighbour list starts the
+// next item at once instead of idling until its CTA's longest list is done.
 template <int Ls, int Ld, int VPT, bool PF = false>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
-                    uint64_t *__restrict__ agg)
+                    uint64_t *__restrict__ agg, unsigned long long *next)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t v = v0 + blockIdx.x * (int64_t)kWarps + warp;
-    if (v >= v1) return;
-    const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-    if (e1 - e0 > split) return;  // heavy vertex: handled by tasks
-    gather_row<Ls, Ld, VPT, PF>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+    int64_t v = next ? 0 : v0 + blockIdx.x * (int64_t)kWarps + warp;
+    while (true) {
+        if (next) {
+            unsigned long long got = 0;
+            if (lane == 0) got = atomicAdd(next, 1ull);
+            v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        }
+        if (v >= v1) return;
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        if (e1 - e0 <= split)  // heavy vertices are summed from their tasks
+            gather_row<Ls, Ld, VPT, PF>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+        if (!next) return;
+    }
 }
 
 template <int Ls, int Ld, int VPT, bool PF = false>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
                     const int64_t *__restrict__ task_e, const uint64_t *__restrict__ X, int64_t R,
-                    uint64_t *__restrict__ partial)
+                    uint64_t *__restrict__ partial, unsigned long long *next)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = t0 + blockIdx.x * (int64_t)kWarps + warp;
-    if (t >= t1) return;
-    gather_row<Ls, Ld, VPT, PF>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
-                                lane);
+    int64_t t = next ? 0 : t0 + blockIdx.x * (int64_t)kWarps + warp;
+    while (true) {
+        if (next) {
+            unsigned long long got = 0;
+            if (lane == 0) got = atomicAdd(next, 1ull);
+            t = t0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        }
+        if (t >= t1) return;
+        gather_row<Ls, Ld, VPT, PF>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
+                                    lane);
+        if (!next) return;
+    }
 }
 
 template <int Ld>
@@ -846,30 +868,56 @@ inline unsigned grid_stride_ctas(int64_t items, int threads)
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
+// persistent grid size: resident CTAs per SM x SMs (queried once per kernel)
+template <typename K>
+unsigned persistent_ctas(K kernel)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;  // (kernel, device) -> CTAs
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(reinterpret_cast<const void *>(kernel), dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return (unsigned)it->second;
+    int per_sm = 1, sms = 152;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n = std::max(1, per_sm) * sms;
+    cache[key] = n;
+    return (unsigned)n;
+}
+
 template <int Ls, int Ld>
 void gather_light_t(cudaStream_t st, bool pf, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
-                    const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg)
+                    const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg, unsigned long long *next)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    if (pf)
-        gather_light_kernel<Ls, Ld, VPT, true><<<grid_for(v1 - v0, kWarps), kWarps * 32, 0, st>>>(v0, v1, split, rp,
-                                                                                               ci, X, R, agg);
-    else
-        gather_light_kernel<Ls, Ld, VPT, false><<<grid_for(v1 - v0, kWarps), kWarps * 32, 0, st>>>(v0, v1, split, rp,
-                                                                                                ci, X, R, agg);
+    if (pf) {
+        auto k = gather_light_kernel<Ls, Ld, VPT, true>;
+        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(v1 - v0, kWarps)) : grid_for(v1 - v0, kWarps);
+        k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next);
+    } else {
+        auto k = gather_light_kernel<Ls, Ld, VPT, false>;
+        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(v1 - v0, kWarps)) : grid_for(v1 - v0, kWarps);
+        k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next);
+    }
 }
 
 template <int Ls, int Ld>
 void gather_tasks_t(cudaStream_t st, bool pf, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
-                    const uint64_t *X, int64_t R, uint64_t *partial)
+                    const uint64_t *X, int64_t R, uint64_t *partial, unsigned long long *next)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    if (pf)
-        gather_tasks_kernel<Ls, Ld, VPT, true><<<grid_for(t1 - t0, kWarps), kWarps * 32, 0, st>>>(t0, t1, ci, te, X,
-                                                                                               R, partial);
-    else
-        gather_tasks_kernel<Ls, Ld, VPT, false><<<grid_for(t1 - t0, kWarps), kWarps * 32, 0, st>>>(t0, t1, ci, te, X,
-                                                                                                R, partial);
+    if (pf) {
+        auto k = gather_tasks_kernel<Ls, Ld, VPT, true>;
+        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(t1 - t0, kWarps)) : grid_for(t1 - t0, kWarps);
+        k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next);
+    } else {
+        auto k = gather_tasks_kernel<Ls, Ld, VPT, false>;
+        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(t1 - t0, kWarps)) : grid_for(t1 - t0, kWarps);
+        k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next);
+    }
 }
 
 #define CC_DISPATCH_L(L, ...)                  \
@@ -899,10 +947,10 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
-                         uint64_t *agg, bool prefetch)
+                         uint64_t *agg, bool prefetch, unsigned long long *next)
 {
     if (v1 <= v0) return;
-#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, v0, v1, split, row_ptr, col_idx, X, R, agg)
+#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, v0, v1, split, row_ptr, col_idx, X, R, agg, next)
     CC_GL(1, 1); CC_GL(1, 2); CC_GL(1, 3); CC_GL(1, 4);
     CC_GL(2, 1); CC_GL(2, 2); CC_GL(2, 3); CC_GL(2, 4);
     CC_GL(3, 1); CC_GL(3, 2); CC_GL(3, 3); CC_GL(3, 4);
@@ -1064,10 +1112,11 @@ void launch_gather_tasks_bulk(cudaStream_t st, int Ls, int Ld, int64_t t0, int64
 }
 
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
-                         const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial, bool prefetch)
+                         const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial, bool prefetch,
+                         unsigned long long *next)
 {
     if (t1 <= t0) return;
-#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, t0, t1, col_idx, task_e, X, R, partial)
+#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, t0, t1, col_idx, task_e, X, R, partial, next)
     CC_GT(1, 1); CC_GT(1, 2); CC_GT(1, 3); CC_GT(1, 4);
     CC_GT(2, 1); CC_GT(2, 2); CC_GT(2, 3); CC_GT(2, 4);
     CC_GT(3, 1); CC_GT(3, 2); CC_GT(3, 3); CC_GT(3, 4);

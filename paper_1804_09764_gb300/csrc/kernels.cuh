@@ -30,14 +30,16 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 // agg[v - v0] = sum_{u in N(v)} X[u]  over rows of R values; light vertices only
 // (deg <= split), heavy ones go through tasks + reduce.
 // prefetch: also request each neighbour row whole into L2 (cp.async.bulk.prefetch)
+// next: zeroed device counter -> persistent grid whose warps pull items from it;
+//       nullptr -> one warp per item
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
-                         int64_t R, uint64_t *agg, bool prefetch = false);
+                         int64_t R, uint64_t *agg, bool prefetch = false, unsigned long long *next = nullptr);
 
 // tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
                          const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
-                         int64_t R, uint64_t *partial, bool prefetch = false);
+                         int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr);
 
 // Vectorised warp versions (16-byte loads, several neighbours in flight) for
 // rows of 1- or 2-limb values; usable when vec_gather_ok(Ls, R).

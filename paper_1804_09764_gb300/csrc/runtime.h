@@ -110,7 +110,7 @@ struct PlanInstance {
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;
     uint64_t off_col = 0, off_hist = 0, off_act[2] = {0, 0}, off_agg = 0, off_partial = 0, off_root = 0,
-             off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0;
+             off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0, off_ctr = 0;
     std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
     // analytic figures
     double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0;

@@ -259,7 +259,7 @@ def test_bulk_and_warp_gathers_agree_with_oracle():
     g = gg.rmat_graph(11, seed=21)
     k, e = gg.template_edges("tree12")
     maps = oracle_maps(g, k, e, 1, 13, range(3))
-    for mode in (0, 1, 2, 3, 4):
+    for mode in (0, 1, 2, 3, 4, 5):
         c = make_ctx(gather_mode=mode, split_threshold=12, batch=2, block_vertices=900)
         gid = c.graph_load(g)
         tid = c.template_load(k, e, 1)
