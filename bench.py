@@ -72,6 +72,34 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def kernel_source_digest() -> str:
+    """Digest of the CUDA sources; DRAM-traffic figures taken with ncu are only
+    used while the kernels are unchanged."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1804_09764_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
+    summary (profiles/traffic_<kernel>_<workload>.json), or None when absent or
+    taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,6 +330,7 @@ def main():
                     help="1 persistent warp gather (default), 5 one-pass warp gather, 0 bulk-copy (TMA) ring, "
                          "2 warp 16-byte vectors, 3 group, 4 persistent warp + L2 prefetch")
     ap.add_argument("--budget-gb", type=float, default=0, help="HBM arena size (0: the workload's)")
+    ap.add_argument("--fused", type=int, default=1, help="1: fused gather + a=1 combine kernel")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=50.0)
@@ -343,7 +372,7 @@ def main():
     budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else wl["budget"]
     budget = min(budget, int(torch.cuda.mem_get_info(local)[0] * 0.9))
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
-                     block_vertices=args.block, gather_mode=args.gather_mode)
+                     block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused)
     gid = ctx.graph_load(g)
     tid = ctx.template_load(k, e, wl["root"])
     info = ctx.plan_info(gid, tid)
@@ -403,7 +432,9 @@ def main():
     dname, d = dom
     achieved = d["bytes"] / d["seconds"] / 1e9 if d["seconds"] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": profiled_traffic(dname, args.workload),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "launches": d["launches"], "avg_launch_ms": 1e3 * d["seconds"] / d["launches"],
                 "share_of_kernel_time": d["seconds"] / sum(v["seconds"] for v in kinds.values())}
     cpu = None
@@ -423,7 +454,7 @@ def main():
                    "workspace_gb": info["workspace_bytes"] / 1e9, "l2": "inputs larger than L2",
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
-                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3),
+                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused),
                    "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row", 2: "warp (16-byte vectors)",
                               3: "group (row per 32-256 threads)", 4: "persistent warp + L2 prefetch",
                               5: "warp per row, one pass"}[args.gather_mode]},

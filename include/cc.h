@@ -72,7 +72,9 @@ typedef struct cc_options {
                                   that fits the budget, at most 16 */
     int32_t block_vertices;    /* vertices per streamed block; 0: largest that fits */
     int32_t use_cuda_graph;    /* 1: capture the per-batch schedule once and replay it */
-    int32_t fused;             /* 1: fused gather+combine kernel for low-degree vertices */
+    int32_t fused;             /* 1 (default): steps that attach a subtree to a single root
+                                  vertex (a = 1) run the gather and the combine as one kernel
+                                  whose neighbour sums go straight into the output row */
     int32_t autotune;          /* 1: time candidate launch shapes on first use of a plan */
     int32_t max_slots;         /* serving: requests in flight at once (default 4) */
     int32_t timing;            /* 1: record per-kernel CUDA-event times (cc_kernel_stats) */

@@ -209,7 +209,7 @@ class Context:
 
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
-                 fused: int = 0, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
+                 fused: int = 1, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
                  stream=None):
         import torch
 

@@ -55,7 +55,7 @@ void cc_default_options(cc_options *opt)
     opt->batch = 0;
     opt->block_vertices = 0;
     opt->use_cuda_graph = 0;
-    opt->fused = 0;
+    opt->fused = 1;
     opt->autotune = 0;
     opt->max_slots = 4;
     opt->timing = 0;

@@ -281,6 +281,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     need_pairs.erase(std::unique(need_pairs.begin(), need_pairs.end()), need_pairs.end());
     uint64_t cbytes = 0;
     for (int h = 1; h <= k; h++) cbytes += rup(T.rm[h].size() * 2);
+    for (int q = 0; q < k; q++) cbytes += rup(T.ad[q].size() * 2);
     std::vector<std::vector<uint32_t>> pt;
     for (auto &hp : need_pairs) {
         pt.push_back(T.pairs(hp.first, hp.second));
@@ -294,6 +295,12 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
         p->d_rm[h] = (uint16_t *)cp;
         CC_CUDA(cudaMemcpyAsync(cp, T.rm[h].data(), T.rm[h].size() * 2, cudaMemcpyHostToDevice, st));
         cp += rup(T.rm[h].size() * 2);
+    }
+    p->d_ad.assign(k + 1, nullptr);
+    for (int q = 0; q < k; q++) {
+        p->d_ad[q] = (uint16_t *)cp;
+        CC_CUDA(cudaMemcpyAsync(cp, T.ad[q].data(), T.ad[q].size() * 2, cudaMemcpyHostToDevice, st));
+        cp += rup(T.ad[q].size() * 2);
     }
     for (size_t i = 0; i < need_pairs.size(); i++) {
         p->d_pairs[need_pairs[i]] = (uint32_t *)cp;
@@ -455,6 +462,30 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                             hrow, out);
                         Ln.end(1, (double)nv * B * ((Ch + binom(k, s.a)) * 8.0 * L + 4.0 * k));
                     }
+                } else if (c->opt.fused && s.a == 1 && !s.reuse_agg &&
+                           !(si + 1 < C.steps.size() && C.steps[si + 1].reuse_agg)) {
+                    // a3 + a4 fused: the aggregate of light vertices goes straight into out
+                    const int Ls = p->chain_L[s.src_chain];
+                    const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
+                    const int64_t R = (int64_t)B * Cps;
+                    const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                    uint64_t *agg = (uint64_t *)W(p->off_agg);
+                    double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                    double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Ch * 8.0 * L;
+                    Ln.begin(K_FUSED);
+                    launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch,
+                                         Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter());
+                    int nl = 1;
+                    if (hv.t1 > hv.t0) {
+                        uint64_t *part = (uint64_t *)W(p->off_partial);
+                        launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
+                                            next_counter());
+                        launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
+                        launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
+                                            agg, out);
+                        nl += 3;
+                    }
+                    Ln.end(nl, bytes);
                 } else {
                     const int Ls = p->chain_L[s.src_chain];
                     const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);

@@ -644,6 +644,96 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
     }
 }
 
+// Fused gather + a = 1 combine (Eq. 1 with T_i' a single vertex): the sum of
+// the neighbour rows agg[T] goes straight to out[T u {col(v)}] (skipped when
+// col(v) is in T); entries S of the output with col(v) not in S are zero.  The
+// aggregate never reaches memory.  Persistent warps pull light vertices from
+// `next`; heavy vertices are left to the task path.
+template <int Ls, int Ld, int VPT>
+__global__ void __launch_bounds__(kWarps * 32)
+gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
+                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
+                     int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
+                     const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col,
+                     uint64_t *__restrict__ out, unsigned long long *next)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t R = (int64_t)B * Cps;
+    while (true) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(next, 1ull);
+        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        if (v >= v1) return;
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select
+        uint64_t *orow = out + (v - v0) * B * Chs * Ld;
+        const uint8_t *cv = col + v * B;
+        // zeros where the vertex's colour is not in S (and in the padding)
+        for (int64_t i = lane; i < (int64_t)B * Chs; i += 32) {
+            const int64_t b = i / Chs, S = i - b * Chs;
+            if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
+                Wide<Ld> z;
+                wzero(z);
+                wstore(orow + i * Ld, z);
+            }
+        }
+        for (int64_t base = 0; base < R; base += 32 * VPT) {
+            Wide<Ld> acc[VPT];
+#pragma unroll
+            for (int q = 0; q < VPT; q++) wzero(acc[q]);
+            for (int64_t e = e0; e < e1; e += 32) {
+                const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+                const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+                int t = 0;
+                for (; t + 2 <= cnt; t += 2) {
+                    const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
+                    const int64_t u1 = __shfl_sync(0xffffffffu, myu, t + 1);
+                    const uint64_t *r0 = X + u0 * R * Ls;
+                    const uint64_t *r1 = X + u1 * R * Ls;
+                    Wide<Ld> x0[VPT], x1[VPT];
+#pragma unroll
+                    for (int q = 0; q < VPT; q++) {
+                        const int64_t c = base + q * 32 + lane;
+                        if (c < R) {
+                            x0[q] = wload<Ls, Ld>(r0 + c * Ls);
+                            x1[q] = wload<Ls, Ld>(r1 + c * Ls);
+                        } else {
+                            wzero(x0[q]);
+                            wzero(x1[q]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < VPT; q++) {
+                        wadd(acc[q], x0[q]);
+                        wadd(acc[q], x1[q]);
+                    }
+                }
+                if (t < cnt) {
+                    const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
+                    const uint64_t *r0 = X + u0 * R * Ls;
+#pragma unroll
+                    for (int q = 0; q < VPT; q++) {
+                        const int64_t c = base + q * 32 + lane;
+                        if (c < R) wadd(acc[q], wload<Ls, Ld>(r0 + c * Ls));
+                    }
+                }
+            }
+            // scatter: agg column T of colouring b lands on T u {col}
+#pragma unroll
+            for (int q = 0; q < VPT; q++) {
+                const int64_t c = base + q * 32 + lane;
+                if (c < R) {
+                    const int64_t b = c / Cps, T = c - b * Cps;
+                    if (T < Cp) {
+                        const uint32_t d = add_p[T * k + cv[b]];
+                        if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Ld, acc[q]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int Ld>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_reduce_kernel(int64_t h0, int64_t h1, int64_t v0, int64_t t0, const int32_t *__restrict__ heavy_v,
@@ -719,6 +809,31 @@ __global__ void combine_select_kernel(int64_t total, int64_t v0, int B, int k, i
 // p = 1: out[S] = sum over c in S of act[S \ {c}] * hist[c].  The h members of S
 // come from the (h, h-1) split table: entry q of S is rank(S \ {c}) | c << 16
 // (the colex rank of {c} is c), laid out [q][S] so a warp reads it coalesced.
+// a = 1 combine for the heavy vertices h0..h1 of the heavy list only (their
+// aggregates come from the task path).
+template <int L>
+__global__ void select_heavy_kernel(int64_t h0, int64_t h1, int64_t v0, const int32_t *__restrict__ heavy_v, int B,
+                                    int k, int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *__restrict__ rm,
+                                    const uint8_t *__restrict__ col, const uint64_t *__restrict__ agg,
+                                    uint64_t *__restrict__ out)
+{
+    const int64_t per = (int64_t)B * Chs;
+    const int64_t total = (h1 - h0) * per;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t hi = h0 + i / per, j = i % per;
+        const int64_t v = heavy_v[hi];
+        const int64_t b = j / Chs, s = j - b * Chs;
+        Wide<L> x;
+        wzero(x);
+        if (s < Ch) {
+            const uint32_t r = rm[s * k + col[v * B + b]];
+            if (r != 0xFFFFu) x = wload<L, L>(agg + ((v - v0) * B * Cps + b * Cps + r) * L);
+        }
+        wstore(out + ((v - v0) * per + j) * L, x);
+    }
+}
+
 template <int L>
 __global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Chs, int64_t Cas, int h,
                                     const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
@@ -1165,6 +1280,46 @@ void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64
     if (total == 0) return;
     CC_DISPATCH_L(L, combine_hist_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
                          total, k, Ch, Chs, Cas, h, pairs, act, hist, out));
+}
+
+namespace {
+
+template <int Ls, int Ld>
+void gather_select_t(cudaStream_t st, int64_t v0, int64_t v1, int64_t split, const int64_t *rp, const int32_t *ci,
+                     const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs,
+                     const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col, uint64_t *out,
+                     unsigned long long *next)
+{
+    constexpr int VPT = Ld <= 2 ? 4 : 2;
+    auto kfn = gather_select_kernel<Ls, Ld, VPT>;
+    const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
+    kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next);
+}
+
+}  // namespace
+
+void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
+                          int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
+                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next)
+{
+    if (v1 <= v0) return;
+#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next)
+    CC_GS(1, 1); CC_GS(1, 2); CC_GS(1, 3); CC_GS(1, 4);
+    CC_GS(2, 1); CC_GS(2, 2); CC_GS(2, 3); CC_GS(2, 4);
+    CC_GS(3, 1); CC_GS(3, 2); CC_GS(3, 3); CC_GS(3, 4);
+    CC_GS(4, 1); CC_GS(4, 2); CC_GS(4, 3); CC_GS(4, 4);
+#undef CC_GS
+}
+
+void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,
+                         int k, int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
+                         const uint64_t *agg, uint64_t *out)
+{
+    const int64_t total = (h1 - h0) * B * Chs;
+    if (total <= 0) return;
+    CC_DISPATCH_L(L, select_heavy_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
+                         h0, h1, v0, heavy_v, B, k, Ch, Chs, Cps, rm, col, agg, out));
 }
 
 int64_t reduce_scratch_ctas() { return 152 * 2; }

@@ -90,6 +90,18 @@ void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0,
 void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64_t Ch, int64_t Chs, int64_t Cas,
                          int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist, uint64_t *out);
 
+// Fused table gather + a = 1 combine for the light vertices of [v0, v1) (persistent
+// warps on the zeroed counter `next`): out[v][b][T u {col}] = sum_u X[u][b][T].
+// add_p: (p -> p+1) add-a-colour ranks; rm_h: remove-a-colour ranks of size h.
+void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
+                          int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
+                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next);
+// a = 1 combine for heavy vertices [h0, h1) of the heavy list (aggregates from the task path)
+void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,
+                         int k, int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
+                         const uint64_t *agg, uint64_t *out);
+
 // totals[b] += sum_v root[v][b]  (root rows hold C(k,k) = 1 column)
 void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_t *root,
                         uint64_t *scratch, int64_t scratch_ctas, uint64_t *totals);

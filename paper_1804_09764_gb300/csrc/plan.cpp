@@ -37,6 +37,16 @@ void SetTables::build(int k_)
         int h = __builtin_popcount(m);
         mask_of_rank[h][colex_rank(m)] = m;
     }
+    ad.assign(k + 1, {});
+    for (int q = 0; q < k; q++) {
+        auto &t = ad[q];
+        t.assign((size_t)binom(k, q) * k, 0xFFFF);
+        for (size_t s = 0; s < mask_of_rank[q].size(); s++) {
+            uint32_t m = mask_of_rank[q][s];
+            for (int c = 0; c < k; c++)
+                if (!(m >> c & 1)) t[s * k + c] = (uint16_t)colex_rank(m | (1u << c));
+        }
+    }
     rm.assign(k + 1, {});
     for (int h = 1; h <= k; h++) {
         auto &t = rm[h];

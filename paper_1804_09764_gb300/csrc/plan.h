@@ -65,6 +65,8 @@ struct SetTables {
     int k = 0;
     // rm[h] : C(k,h) x k entries, rank of S \ {c} in the (h-1)-sets, or 0xFFFF if c not in S
     std::vector<std::vector<uint16_t>> rm;
+    // ad[p] : C(k,p) x k entries, rank of T u {c} in the (p+1)-sets, or 0xFFFF if c in T
+    std::vector<std::vector<uint16_t>> ad;
     // members of each set by rank, per size (bitmask)
     std::vector<std::vector<uint32_t>> mask_of_rank;
     void build(int k_);

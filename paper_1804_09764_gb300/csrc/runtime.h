@@ -106,6 +106,7 @@ struct PlanInstance {
     // device constants (arena): rm tables per h, pair tables per (h, a)
     void *consts = nullptr;
     std::vector<uint16_t *> d_rm;               // [h]
+    std::vector<uint16_t *> d_ad;               // [p] (fused gather + select steps)
     std::map<std::pair<int, int>, uint32_t *> d_pairs;
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;

@@ -293,3 +293,18 @@ def test_autotuned_plan_matches_oracle():
         res = c.count(gid, tid, seed=5, n_iter=4, first_iter=first, want_maps=True)
         assert res["maps"] == oracle_maps(g, k, e, 1, 5, range(first, first + 4))
     c.close()
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_fused_and_unfused_gather_select(fused):
+    # a = 1 steps: fused gather + select kernel against the separate kernels, with
+    # heavy vertices (split 10), vertex blocks and batches
+    g = gg.rmat_graph(11, seed=44)
+    k, e = gg.template_edges("tree12")
+    maps = oracle_maps(g, k, e, 1, 17, range(3))
+    c = make_ctx(fused=fused, split_threshold=10, batch=2, block_vertices=777)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 1)
+    res = c.count(gid, tid, seed=17, n_iter=3, want_maps=True)
+    assert res["maps"] == maps
+    c.close()
