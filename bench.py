@@ -327,10 +327,11 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=1,
-                    help="1 persistent warp gather (default), 5 one-pass warp gather, 0 bulk-copy (TMA) ring, "
-                         "2 warp 16-byte vectors, 3 group, 4 persistent warp + L2 prefetch")
+                    help="1 persistent warp gather, 4 rows in flight (default); 6: 2 rows in flight; 5 one-pass warp "
+                         "gather; 0 bulk-copy (TMA) ring; 2 warp 16-byte vectors; 3 group; 4 as 6 + L2 prefetch")
     ap.add_argument("--budget-gb", type=float, default=0, help="HBM arena size (0: the workload's)")
     ap.add_argument("--fused", type=int, default=1, help="1: fused gather + a=1 combine kernel")
+    ap.add_argument("--autotune", type=int, default=0, help="1: time every gather variant per site on the first pass")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=50.0)
@@ -372,7 +373,8 @@ def main():
     budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else wl["budget"]
     budget = min(budget, int(torch.cuda.mem_get_info(local)[0] * 0.9))
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
-                     block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused)
+                     block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused,
+                     autotune=args.autotune)
     gid = ctx.graph_load(g)
     tid = ctx.template_load(k, e, wl["root"])
     info = ctx.plan_info(gid, tid)
@@ -454,10 +456,11 @@ def main():
                    "workspace_gb": info["workspace_bytes"] / 1e9, "l2": "inputs larger than L2",
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
-                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused),
-                   "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row", 2: "warp (16-byte vectors)",
-                              3: "group (row per 32-256 threads)", 4: "persistent warp + L2 prefetch",
-                              5: "warp per row, one pass"}[args.gather_mode]},
+                   "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused), "autotune": bool(args.autotune),
+                   "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row, 4 rows in flight",
+                              2: "warp (16-byte vectors)", 3: "group (row per 32-256 threads)",
+                              4: "persistent warp + L2 prefetch", 5: "warp per row, one pass",
+                              6: "persistent warp per row, 2 rows in flight"}[args.gather_mode]},
         "hbm_frac_step": info["algorithmic_bytes_per_colouring"] * n_iter * args.steps / elapsed / 1e9 / peak,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -79,10 +79,11 @@ typedef struct cc_options {
     int32_t max_slots;         /* serving: requests in flight at once (default 4) */
     int32_t timing;            /* 1: record per-kernel CUDA-event times (cc_kernel_stats) */
     int32_t gather_mode;       /* table-gather kernel: 1 (default): warp per row, persistent
-                                  warps pulling rows from a counter; 5: warp per row, one
+                                  warps pulling rows from a counter, 4 neighbour rows in
+                                  flight; 6: as 1 with 2 rows in flight; 5: warp per row, one
                                   pass (no counter); 0: bulk-copy (TMA) ring for rows of
                                   >= 1 KiB of 1- or 2-limb values; 2: warp per row, 16-byte
-                                  vectors; 3: 32..256 threads per row; 4: as 1 plus whole-row
+                                  vectors; 3: 32..256 threads per row; 4: as 6 plus whole-row
                                   L2 prefetch.  With autotune = 1 each gather site picks the
                                   fastest. */
     int32_t reserved[5];

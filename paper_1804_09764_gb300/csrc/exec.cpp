@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "runtime.h"
@@ -473,13 +475,31 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
                     double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Ch * 8.0 * L;
                     Ln.begin(K_FUSED);
-                    launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch,
-                                         Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter());
-                    int nl = 1;
+                    const auto site = std::make_pair((int)ci, (int)si);
+                    auto fused_run = [&](int nb) {
+                        launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch,
+                                             Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(), nb);
+                    };
+                    int nl = 1, nb_tasks = 2;
+                    if (tune) {
+                        for (int nb : {2, 4}) {  // the default (4) last
+                            PlanInstance::Trial tr{(int)ci, (int)si, nb, nullptr, nullptr};
+                            cudaEventCreate(&tr.a);
+                            cudaEventCreate(&tr.b);
+                            cudaEventRecord(tr.a, st);
+                            fused_run(nb);
+                            cudaEventRecord(tr.b, st);
+                            p->trials.push_back(tr);
+                        }
+                    } else {
+                        auto it = p->site_mode.find(site);
+                        nb_tasks = (it != p->site_mode.end() && it->second == 2) ? 2 : 4;
+                        fused_run(nb_tasks);
+                    }
                     if (hv.t1 > hv.t0) {
                         uint64_t *part = (uint64_t *)W(p->off_partial);
                         launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                            next_counter());
+                                            next_counter(), nb_tasks);
                         launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                         launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
                                             agg, out);
@@ -512,7 +532,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 launch_gather_light_vec(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
                             else
                                 launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
-                                                    gm == 4, gm == 5 ? nullptr : next_counter());
+                                                    gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4);
                             int n = 1;
                             if (hv.t1 > hv.t0) {
                                 uint64_t *part = (uint64_t *)W(p->off_partial);
@@ -526,7 +546,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                     launch_gather_tasks_vec(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
                                 else
                                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
-                                                        gm == 4, gm == 5 ? nullptr : next_counter());
+                                                        gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4);
                                 launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
                                 n += 2;
@@ -537,7 +557,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         const auto site = std::make_pair((int)ci, (int)si);
                         if (tune) {
                             // every variant computes the same sums; the last one run leaves agg
-                            for (int gm : {0, 2, 3, 4, 5, 1}) {  // the default (1) last
+                            for (int gm : {0, 2, 3, 4, 5, 6, 1}) {  // the default (1) last
                                 if ((gm == 0 && !bulk_gather_ok(Ls, R)) || ((gm == 2 || gm == 3) && !vec_gather_ok(Ls, R)))
                                     continue;
                                 PlanInstance::Trial tr{(int)ci, (int)si, gm, nullptr, nullptr};
@@ -626,12 +646,18 @@ static cc_status finish_tuning(Ctx *c, PlanInstance *p, cudaStream_t st)
     }
     cudaGetLastError();
     p->trials.clear();
+    const bool log = std::getenv("CC_TUNE_LOG") != nullptr;
     for (auto &site : t) {
         int best = c->opt.gather_mode;
         double bt = 1e300;
         for (auto &m : site.second)
             if (m.second < bt) bt = m.second, best = m.first;
         p->site_mode[site.first] = best;
+        if (log) {
+            std::fprintf(stderr, "cc autotune: chain %d step %d:", site.first.first, site.first.second);
+            for (auto &m : site.second) std::fprintf(stderr, " mode %d %.3f ms;", m.first, m.second);
+            std::fprintf(stderr, " -> %d\n", best);
+        }
     }
     p->tuned = true;
     c->tuned_modes[std::make_tuple(p->graph_id, p->tmpl_id, p->B)] = p->site_mode;

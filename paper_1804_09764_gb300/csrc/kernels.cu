@@ -79,11 +79,56 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1):
+// neighbour ids are fetched 32 at a time and broadcast with shuffles, and NB
+// neighbours' values are loaded before any is added (NB * VPT loads in flight
+// per lane).
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                                const uint64_t *__restrict__ X, int64_t R, int64_t base,
+                                                Wide<Ld> (&acc)[VPT], int lane)
+{
+    for (int64_t e = e0; e < e1; e += 32) {
+        const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+        const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+        int t = 0;
+        for (; t + NB <= cnt; t += NB) {
+            Wide<Ld> x[NB][VPT];
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                const int64_t u = __shfl_sync(0xffffffffu, myu, t + j);
+                const uint64_t *row = X + u * R * Ls;
+#pragma unroll
+                for (int q = 0; q < VPT; q++) {
+                    const int64_t c = base + q * 32 + lane;
+                    if (c < R)
+                        x[j][q] = wload<Ls, Ld>(row + c * Ls);
+                    else
+                        wzero(x[j][q]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NB; j++)
+#pragma unroll
+                for (int q = 0; q < VPT; q++) wadd(acc[q], x[j][q]);
+        }
+        for (; t < cnt; t++) {
+            const int64_t u = __shfl_sync(0xffffffffu, myu, t);
+            const uint64_t *row = X + u * R * Ls;
+#pragma unroll
+            for (int q = 0; q < VPT; q++) {
+                const int64_t c = base + q * 32 + lane;
+                if (c < R) wadd(acc[q], wload<Ls, Ld>(row + c * Ls));
+            }
+        }
+    }
+}
+
 // Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.
 // Lane `lane` owns values base + q*32 + lane, q < VPT; the neighbour ids are
 // fetched 32 at a time and broadcast with shuffles; two neighbours are loaded
 // before adding so 2*VPT loads are in flight per lane.
-template <int Ls, int Ld, int VPT, bool PF = false>
+template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
                                            const uint64_t *__restrict__ X, int64_t R,
                                            uint64_t *__restrict__ out_row, int lane)
@@ -92,45 +137,10 @@ __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, 
         Wide<Ld> acc[VPT];
 #pragma unroll
         for (int q = 0; q < VPT; q++) wzero(acc[q]);
-        for (int64_t e = e0; e < e1; e += 32) {
-            const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
-            const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
-            if (PF && base == 0 && R > 32 * VPT && lane < cnt && (R * Ls) % 2 == 0)
-                prefetch_l2(X + (int64_t)myu * R * Ls, (uint32_t)(R * Ls * 8));
-            int t = 0;
-            for (; t + 2 <= cnt; t += 2) {
-                const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
-                const int64_t u1 = __shfl_sync(0xffffffffu, myu, t + 1);
-                const uint64_t *r0 = X + u0 * R * Ls;
-                const uint64_t *r1 = X + u1 * R * Ls;
-                Wide<Ld> x0[VPT], x1[VPT];
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    const int64_t c = base + q * 32 + lane;
-                    if (c < R) {
-                        x0[q] = wload<Ls, Ld>(r0 + c * Ls);
-                        x1[q] = wload<Ls, Ld>(r1 + c * Ls);
-                    } else {
-                        wzero(x0[q]);
-                        wzero(x1[q]);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    wadd(acc[q], x0[q]);
-                    wadd(acc[q], x1[q]);
-                }
-            }
-            if (t < cnt) {
-                const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
-                const uint64_t *r0 = X + u0 * R * Ls;
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    const int64_t c = base + q * 32 + lane;
-                    if (c < R) wadd(acc[q], wload<Ls, Ld>(r0 + c * Ls));
-                }
-            }
-        }
+        if (PF && base == 0 && R > 32 * VPT && (R * Ls) % 2 == 0)
+            for (int64_t e = e0 + lane; e < e1; e += 32)
+                prefetch_l2(X + (int64_t)col_idx[e] * R * Ls, (uint32_t)(R * Ls * 8));
+        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
 #pragma unroll
         for (int q = 0; q < VPT; q++) {
             const int64_t c = base + q * 32 + lane;
@@ -601,7 +611,7 @@ gather_group_kernel(int64_t a, int64_t b, int G, int tasks, int64_t split, const
 // pass); otherwise the grid is persistent and each warp pulls its next item
 // from the counter, so a warp that finishes a short neighbour list starts the
 // next item at once instead of idling until its CTA's longest list is done.
-template <int Ls, int Ld, int VPT, bool PF = false>
+template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
@@ -618,12 +628,12 @@ gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__rest
         if (v >= v1) return;
         const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
         if (e1 - e0 <= split)  // heavy vertices are summed from their tasks
-            gather_row<Ls, Ld, VPT, PF>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+            gather_row<Ls, Ld, VPT, PF, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
         if (!next) return;
     }
 }
 
-template <int Ls, int Ld, int VPT, bool PF = false>
+template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
                     const int64_t *__restrict__ task_e, const uint64_t *__restrict__ X, int64_t R,
@@ -638,8 +648,8 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
             t = t0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
         }
         if (t >= t1) return;
-        gather_row<Ls, Ld, VPT, PF>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, partial + (t - t0) * R * Ld,
-                                    lane);
+        gather_row<Ls, Ld, VPT, PF, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R,
+                                        partial + (t - t0) * R * Ld, lane);
         if (!next) return;
     }
 }
@@ -649,7 +659,7 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
 // col(v) is in T); entries S of the output with col(v) not in S are zero.  The
 // aggregate never reaches memory.  Persistent warps pull light vertices from
 // `next`; heavy vertices are left to the task path.
-template <int Ls, int Ld, int VPT>
+template <int Ls, int Ld, int VPT, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                      const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
@@ -681,43 +691,7 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
             Wide<Ld> acc[VPT];
 #pragma unroll
             for (int q = 0; q < VPT; q++) wzero(acc[q]);
-            for (int64_t e = e0; e < e1; e += 32) {
-                const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
-                const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
-                int t = 0;
-                for (; t + 2 <= cnt; t += 2) {
-                    const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
-                    const int64_t u1 = __shfl_sync(0xffffffffu, myu, t + 1);
-                    const uint64_t *r0 = X + u0 * R * Ls;
-                    const uint64_t *r1 = X + u1 * R * Ls;
-                    Wide<Ld> x0[VPT], x1[VPT];
-#pragma unroll
-                    for (int q = 0; q < VPT; q++) {
-                        const int64_t c = base + q * 32 + lane;
-                        if (c < R) {
-                            x0[q] = wload<Ls, Ld>(r0 + c * Ls);
-                            x1[q] = wload<Ls, Ld>(r1 + c * Ls);
-                        } else {
-                            wzero(x0[q]);
-                            wzero(x1[q]);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < VPT; q++) {
-                        wadd(acc[q], x0[q]);
-                        wadd(acc[q], x1[q]);
-                    }
-                }
-                if (t < cnt) {
-                    const int64_t u0 = __shfl_sync(0xffffffffu, myu, t);
-                    const uint64_t *r0 = X + u0 * R * Ls;
-#pragma unroll
-                    for (int q = 0; q < VPT; q++) {
-                        const int64_t c = base + q * 32 + lane;
-                        if (c < R) wadd(acc[q], wload<Ls, Ld>(r0 + c * Ls));
-                    }
-                }
-            }
+            accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
             // scatter: agg column T of colouring b lands on T u {col}
 #pragma unroll
             for (int q = 0; q < VPT; q++) {
@@ -1004,35 +978,25 @@ unsigned persistent_ctas(K kernel)
 }
 
 template <int Ls, int Ld>
-void gather_light_t(cudaStream_t st, bool pf, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
+void gather_light_t(cudaStream_t st, bool pf, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                     const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg, unsigned long long *next)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    if (pf) {
-        auto k = gather_light_kernel<Ls, Ld, VPT, true>;
-        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(v1 - v0, kWarps)) : grid_for(v1 - v0, kWarps);
-        k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next);
-    } else {
-        auto k = gather_light_kernel<Ls, Ld, VPT, false>;
-        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(v1 - v0, kWarps)) : grid_for(v1 - v0, kWarps);
-        k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next);
-    }
+    auto k = pf ? gather_light_kernel<Ls, Ld, VPT, true, 2>
+                : (nb == 4 ? gather_light_kernel<Ls, Ld, VPT, false, 4> : gather_light_kernel<Ls, Ld, VPT, false, 2>);
+    const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(v1 - v0, kWarps)) : grid_for(v1 - v0, kWarps);
+    k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next);
 }
 
 template <int Ls, int Ld>
-void gather_tasks_t(cudaStream_t st, bool pf, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
+void gather_tasks_t(cudaStream_t st, bool pf, int nb, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
                     const uint64_t *X, int64_t R, uint64_t *partial, unsigned long long *next)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    if (pf) {
-        auto k = gather_tasks_kernel<Ls, Ld, VPT, true>;
-        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(t1 - t0, kWarps)) : grid_for(t1 - t0, kWarps);
-        k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next);
-    } else {
-        auto k = gather_tasks_kernel<Ls, Ld, VPT, false>;
-        const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(t1 - t0, kWarps)) : grid_for(t1 - t0, kWarps);
-        k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next);
-    }
+    auto k = pf ? gather_tasks_kernel<Ls, Ld, VPT, true, 2>
+                : (nb == 4 ? gather_tasks_kernel<Ls, Ld, VPT, false, 4> : gather_tasks_kernel<Ls, Ld, VPT, false, 2>);
+    const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(t1 - t0, kWarps)) : grid_for(t1 - t0, kWarps);
+    k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next);
 }
 
 #define CC_DISPATCH_L(L, ...)                  \
@@ -1062,10 +1026,10 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
-                         uint64_t *agg, bool prefetch, unsigned long long *next)
+                         uint64_t *agg, bool prefetch, unsigned long long *next, int nb)
 {
     if (v1 <= v0) return;
-#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, v0, v1, split, row_ptr, col_idx, X, R, agg, next)
+#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, nb, v0, v1, split, row_ptr, col_idx, X, R, agg, next)
     CC_GL(1, 1); CC_GL(1, 2); CC_GL(1, 3); CC_GL(1, 4);
     CC_GL(2, 1); CC_GL(2, 2); CC_GL(2, 3); CC_GL(2, 4);
     CC_GL(3, 1); CC_GL(3, 2); CC_GL(3, 3); CC_GL(3, 4);
@@ -1228,10 +1192,10 @@ void launch_gather_tasks_bulk(cudaStream_t st, int Ls, int Ld, int64_t t0, int64
 
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
                          const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial, bool prefetch,
-                         unsigned long long *next)
+                         unsigned long long *next, int nb)
 {
     if (t1 <= t0) return;
-#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, t0, t1, col_idx, task_e, X, R, partial, next)
+#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, nb, t0, t1, col_idx, task_e, X, R, partial, next)
     CC_GT(1, 1); CC_GT(1, 2); CC_GT(1, 3); CC_GT(1, 4);
     CC_GT(2, 1); CC_GT(2, 2); CC_GT(2, 3); CC_GT(2, 4);
     CC_GT(3, 1); CC_GT(3, 2); CC_GT(3, 3); CC_GT(3, 4);
@@ -1285,13 +1249,13 @@ void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64
 namespace {
 
 template <int Ls, int Ld>
-void gather_select_t(cudaStream_t st, int64_t v0, int64_t v1, int64_t split, const int64_t *rp, const int32_t *ci,
-                     const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs,
-                     const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col, uint64_t *out,
+void gather_select_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
+                     const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
+                     int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col, uint64_t *out,
                      unsigned long long *next)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
-    auto kfn = gather_select_kernel<Ls, Ld, VPT>;
+    auto kfn = nb == 4 ? gather_select_kernel<Ls, Ld, VPT, 4> : gather_select_kernel<Ls, Ld, VPT, 2>;
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next);
 }
@@ -1301,10 +1265,10 @@ void gather_select_t(cudaStream_t st, int64_t v0, int64_t v1, int64_t split, con
 void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                           const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
-                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next)
+                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next, int nb)
 {
     if (v1 <= v0) return;
-#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next)
+#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next)
     CC_GS(1, 1); CC_GS(1, 2); CC_GS(1, 3); CC_GS(1, 4);
     CC_GS(2, 1); CC_GS(2, 2); CC_GS(2, 3); CC_GS(2, 4);
     CC_GS(3, 1); CC_GS(3, 2); CC_GS(3, 3); CC_GS(3, 4);

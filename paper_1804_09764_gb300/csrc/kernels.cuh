@@ -32,14 +32,17 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 // prefetch: also request each neighbour row whole into L2 (cp.async.bulk.prefetch)
 // next: zeroed device counter -> persistent grid whose warps pull items from it;
 //       nullptr -> one warp per item
+// nb: neighbour rows loaded before adding (2 or 4)
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
-                         int64_t R, uint64_t *agg, bool prefetch = false, unsigned long long *next = nullptr);
+                         int64_t R, uint64_t *agg, bool prefetch = false, unsigned long long *next = nullptr,
+                         int nb = 4);
 
 // tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
                          const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
-                         int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr);
+                         int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr,
+                         int nb = 4);
 
 // Vectorised warp versions (16-byte loads, several neighbours in flight) for
 // rows of 1- or 2-limb values; usable when vec_gather_ok(Ls, R).
@@ -96,7 +99,8 @@ void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64
 void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                           const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
-                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next);
+                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next,
+                          int nb = 4);
 // a = 1 combine for heavy vertices [h0, h1) of the heavy list (aggregates from the task path)
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,
                          int k, int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
