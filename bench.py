@@ -73,14 +73,14 @@ def max_over_ranks(x: float, device=None) -> float:
 
 
 def kernel_source_digest() -> str:
-    """Digest of the CUDA sources; DRAM-traffic figures taken with ncu are only
-    used while the kernels are unchanged."""
+    """Digest of the CUDA sources and of the planner/executor; DRAM-traffic
+    figures taken with ncu are only used while these are unchanged."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_09764_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
+    for name in sorted(os.listdir(csrc)):  # kernels, and the planner/executor that decide their launches
+        if name.endswith((".cu", ".cuh")) or name in ("exec.cpp", "plan.cpp"):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -260,7 +260,7 @@ def run_serving(args):
     rng = np.random.default_rng(2024)
     scales = list(range(16, args.serve_max_scale + 1))
     graphs = [gg.rmat_graph(sc, seed=sc) for sc in scales] + [gg.er_graph(1 << 20, 16, seed=7)]
-    budget = min(int(args.budget_gb * (1 << 30)) if args.budget_gb else 200 << 30,
+    budget = min(int(args.budget_gb * (1 << 30)) if args.budget_gb else 250 << 30,
                  int(torch.cuda.mem_get_info(0)[0] * 0.9))
     ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
     gids = [ctx.graph_load(g) for g in graphs]
@@ -277,26 +277,35 @@ def run_serving(args):
     # updates per request (same U definition as the counting metric)
     for r in reqs:
         r["U"] = plan_updates_host(graphs[r["g"]], r["k"], r["e"], 0) * r["n_iter"]
-    # plain path: one request after another through cc_count
+    # plain path: one request after another through cc_count; a request whose
+    # tables cannot fit the budget is refused (CC_ERR_BUDGET) on both paths
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for r in reqs:
-        ctx.count(gids[r["g"]], r["tid"], seed=r["seed"], n_iter=r["n_iter"])
+        try:
+            r["plain"] = ctx.count(gids[r["g"]], r["tid"], seed=r["seed"], n_iter=r["n_iter"])["counts"]
+        except cc.CCError as e:
+            r["plain"] = e.status
     plain_s = time.perf_counter() - t0
     # served: submit at arrival times, collect results
     start = time.perf_counter()
     ids = []
-    lat = []
     for r in reqs:
         now = time.perf_counter() - start
         if r["at"] > now:
             time.sleep(r["at"] - now)
         ids.append((ctx.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"]), r))
+    mismatched = 0
     for rid, r in ids:
-        ctx.wait(rid, r["n_iter"], timeout_s=3600)
+        try:
+            got = ctx.wait(rid, r["n_iter"], timeout_s=3600)["counts"]
+        except cc.CCError as e:
+            got = e.status
+        mismatched += got != r["plain"]
     served_s = time.perf_counter() - start
     st = ctx.serve_stats()
-    U = sum(r["U"] for r in reqs)
+    ok = [r for r in reqs if not isinstance(r["plain"], int)]
+    U = sum(r["U"] for r in ok)
     line = {"metric": "served_p99_latency_s", "value": st["p99_latency_s"], "unit": "s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": served_s * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64/u128/u192", "data": "synthetic",
@@ -306,7 +315,8 @@ def run_serving(args):
             "serving": {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
                         "mean_latency_s": st["mean_latency_s"], "completed": st["completed"],
                         "requests_per_s": args.requests / served_s, "updates_per_s": U / served_s,
-                        "busy_s": st["busy_seconds"], "admissions_deferred": st["admissions_deferred"]},
+                        "busy_s": st["busy_seconds"], "admissions_deferred": st["admissions_deferred"],
+                        "refused_over_budget": len(reqs) - len(ok), "results_differ_from_plain": mismatched},
             "plain_sequential": {"seconds": plain_s, "requests_per_s": args.requests / plain_s,
                                  "updates_per_s": U / plain_s}}
     print(json.dumps(line), flush=True)

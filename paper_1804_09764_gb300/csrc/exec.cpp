@@ -189,37 +189,92 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     p->tmpl_id = tid;
     std::string err;
     double avg = g->n_act ? (double)g->nnz / g->n_act : 1.0;
-    int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &p->tp, &err);
-    if (rc) return fail(rc, err);
+    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
+        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
+    // Integer widths of a partition: every chain at the smallest L with
+    // max_v H(v) < 2^(64 L), capped at the root's L (which covers sum_v H).
+    auto widths = [&](const TemplatePlan &tp, std::vector<int> *chain_L, int *L_root) -> cc_status {
+        const int nc = (int)tp.chains.size();
+        chain_L->assign(nc, 1);
+        *L_root = 1;
+        if (tp.k < 2 || g->n_act == 0) return CC_OK;
+        if (width_bits != 0) {
+            *L_root = width_bits / 64;
+            for (auto &L : *chain_L) L = *L_root;
+            return CC_OK;
+        }
+        std::vector<double> l2max;
+        double l2sum;
+        CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum));
+        const int rb = bits_from_log2(l2sum);
+        if (rb > 256)
+            return fail(CC_ERR_WIDTH, "exact counts may need " + std::to_string(rb) +
+                                          " bits (> 256); request a fixed width_bits for residues");
+        *L_root = (rb + 63) / 64;
+        for (int i = 0; i < nc; i++) {
+            const int b = bits_from_log2(l2max[i]);
+            (*chain_L)[i] = tp.chains[i].is_root ? *L_root : std::min(*L_root, (b + 63) / 64);
+        }
+        return CC_OK;
+    };
+    // modelled time of a partition: bytes of its gathers and table writes at
+    // their widths over HBM, plus its combine work (a multiply-add costs ~L^2)
+    auto model = [&](const TemplatePlan &tp, const std::vector<int> &chain_L) {
+        const double nnz = (double)g->nnz, na = (double)g->n_act;
+        double bytes = 0, work = 0;
+        for (size_t i = 0; i < tp.chains.size(); i++) {
+            const auto &C = tp.chains[i];
+            const double L = chain_L[i];
+            if (!C.is_root) bytes += na * (double)col_stride(binom(tp.k, C.size)) * 8.0 * L;
+            for (auto &s : C.steps) {
+                if (s.src_chain >= 0 && !s.reuse_agg)
+                    bytes += nnz * (double)col_stride(binom(tp.k, s.p)) * 8.0 * chain_L[s.src_chain];
+                const double pr = s.a == 1 ? (double)binom(tp.k, s.h)
+                                           : (double)binom(tp.k, s.h) * (double)binom(s.h, s.a);
+                work += na * pr * L * L;
+            }
+        }
+        return bytes / 6.0e12 + work / 3.0e11;
+    };
+    if (t->root_req >= 0 || t->k <= 2 || g->n_act == 0) {
+        int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &p->tp, &err);
+        if (rc) return fail(rc, err);
+        CC_TRY(widths(p->tp, &p->chain_L, &p->L_root));
+    } else {
+        // the planner's root: the least modelled time with the widths each root
+        // needs.  The model at 64-bit widths is a lower bound, so roots are tried
+        // in its order and the search stops once that bound reaches the best.
+        std::vector<std::pair<double, int>> rank;
+        for (int r = 0; r < t->k; r++) {
+            TemplatePlan tp;
+            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err);
+            if (rc) return fail(rc, err);
+            rank.push_back({model(tp, std::vector<int>(tp.chains.size(), 1)), r});
+        }
+        std::sort(rank.begin(), rank.end());
+        double best = 1e300;
+        for (size_t ri = 0; ri < rank.size() && rank[ri].first < best; ri++) {
+            const int r = rank[ri].second;
+            TemplatePlan tp;
+            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err);
+            if (rc) return fail(rc, err);
+            std::vector<int> cl;
+            int lr = 1;
+            CC_TRY(widths(tp, &cl, &lr));
+            const double m = model(tp, cl);
+            if (m < best) {
+                best = m;
+                p->tp = tp;
+                p->chain_L = cl;
+                p->L_root = lr;
+            }
+        }
+    }
     const TemplatePlan &tp = p->tp;
     const int k = tp.k;
     const int nc = (int)tp.chains.size();
-    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
-        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
     p->width_bits = width_bits;
     p->exact = width_bits == 0;
-    p->chain_L.assign(nc, 1);
-    if (k >= 2 && g->n_act > 0) {
-        if (width_bits == 0) {
-            std::vector<double> l2max;
-            double l2sum;
-            CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum));
-            int rb = bits_from_log2(l2sum);
-            if (rb > 256)
-                return fail(CC_ERR_WIDTH, "exact counts may need " + std::to_string(rb) +
-                                              " bits (> 256); request a fixed width_bits for residues");
-            p->L_root = (rb + 63) / 64;
-            for (int i = 0; i < nc; i++) {
-                int b = bits_from_log2(l2max[i]);
-                p->chain_L[i] = tp.chains[i].is_root ? p->L_root : std::min(p->L_root, (b + 63) / 64);
-            }
-        } else {
-            p->L_root = width_bits / 64;
-            for (auto &L : p->chain_L) L = p->L_root;
-        }
-    } else {
-        p->L_root = 1;
-    }
     p->Lmax = *std::max_element(p->chain_L.begin(), p->chain_L.end());
     // split threshold and batch / block size under the budget
     p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : 1024;
