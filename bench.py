@@ -342,6 +342,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=0, help="HBM arena size (0: the workload's)")
     ap.add_argument("--fused", type=int, default=1, help="1: fused gather + a=1 combine kernel")
     ap.add_argument("--autotune", type=int, default=0, help="1: time every gather variant per site on the first pass")
+    ap.add_argument("--vertex-order", type=int, default=0, help="0: by decreasing degree, 1: input order")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=50.0)
@@ -384,7 +385,7 @@ def main():
     budget = min(budget, int(torch.cuda.mem_get_info(local)[0] * 0.9))
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
                      block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused,
-                     autotune=args.autotune)
+                     autotune=args.autotune, vertex_order=args.vertex_order)
     gid = ctx.graph_load(g)
     tid = ctx.template_load(k, e, wl["root"])
     info = ctx.plan_info(gid, tid)
@@ -467,6 +468,7 @@ def main():
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
                    "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused), "autotune": bool(args.autotune),
+                   "vertex_order": "degree" if args.vertex_order == 0 else "input",
                    "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row, 4 rows in flight",
                               2: "warp (16-byte vectors)", 3: "group (row per 32-256 threads)",
                               4: "persistent warp + L2 prefetch", 5: "warp per row, one pass",

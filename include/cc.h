@@ -86,7 +86,9 @@ typedef struct cc_options {
                                   vectors; 3: 32..256 threads per row; 4: as 6 plus whole-row
                                   L2 prefetch.  With autotune = 1 each gather site picks the
                                   fastest. */
-    int32_t reserved[5];
+    int32_t vertex_order;      /* 0 (default): active vertices numbered by decreasing degree
+                                  (hub rows contiguous); 1: input order */
+    int32_t reserved[4];
 } cc_options;
 
 void cc_default_options(cc_options *opt);

@@ -49,7 +49,8 @@ class cc_options(ctypes.Structure):
                 ("split_threshold", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("block_vertices", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("autotune", ctypes.c_int32), ("max_slots", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class cc_result(ctypes.Structure):
@@ -210,7 +211,7 @@ class Context:
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
                  fused: int = 1, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
-                 stream=None):
+                 vertex_order: int = 0, stream=None):
         import torch
 
         lib = load_library()
@@ -240,6 +241,7 @@ class Context:
         opt.max_slots = max_slots
         opt.timing = timing
         opt.gather_mode = gather_mode
+        opt.vertex_order = vertex_order
         torch.cuda.synchronize(device)
         h = ctypes.c_void_p()
         _check(lib.cc_create(ctypes.byref(h), ctypes.byref(opt)))

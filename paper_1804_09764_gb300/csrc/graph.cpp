@@ -79,17 +79,23 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
         }
         CC_TRY(validate_host(n, rp.data(), p));
     }
-    // compact numbering: drop isolated vertices (they are in no embedding when k >= 2)
-    g->h_new_id.assign(n, -1);
+    // Compact numbering: isolated vertices are dropped (they are in no embedding
+    // when k >= 2).  By default the active vertices are also ordered by
+    // decreasing degree, so the rows of the hub vertices -- the rows read most
+    // often by the gathers -- sit together at the start of every table.
+    const bool by_degree = c->opt.vertex_order == 0;
     std::vector<int64_t> orig;
-    g->h_row_ptr.clear();
-    g->h_row_ptr.push_back(0);
-    for (int64_t v = 0; v < n; v++) {
-        int64_t d = rp[v + 1] - rp[v];
-        if (d == 0) continue;
-        g->h_new_id[v] = (int32_t)orig.size();
-        orig.push_back(v);
-        g->h_row_ptr.push_back(rp[v + 1]);  // isolated vertices hold no edges: offsets unchanged
+    for (int64_t v = 0; v < n; v++)
+        if (rp[v + 1] > rp[v]) orig.push_back(v);
+    if (by_degree)
+        std::stable_sort(orig.begin(), orig.end(),
+                         [&](int64_t x, int64_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+    g->h_new_id.assign(n, -1);
+    g->h_row_ptr.assign(orig.size() + 1, 0);
+    for (size_t i = 0; i < orig.size(); i++) {
+        const int64_t v = orig[i], d = rp[v + 1] - rp[v];
+        g->h_new_id[v] = (int32_t)i;
+        g->h_row_ptr[i + 1] = g->h_row_ptr[i] + d;
         g->max_degree = std::max(g->max_degree, d);
     }
     g->n_act = (int64_t)orig.size();
@@ -101,13 +107,17 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
     g->orig = (int64_t *)A(sizeof(int64_t) * std::max<int64_t>(g->n_act, 1));
     int32_t *d_new = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(n, 1));
     int32_t *d_src = nullptr;
+    int64_t *d_old_rp = nullptr;
     if (nnz > 0 && !ci_dev) d_src = (int32_t *)A(sizeof(int32_t) * nnz);
-    if (!g->row_ptr || !g->col_idx || !g->orig || !d_new || (nnz > 0 && !ci_dev && !d_src)) {
+    if (nnz > 0 && by_degree) d_old_rp = (int64_t *)A(sizeof(int64_t) * (n + 1));
+    if (!g->row_ptr || !g->col_idx || !g->orig || !d_new || (nnz > 0 && !ci_dev && !d_src) ||
+        (nnz > 0 && by_degree && !d_old_rp)) {
         c->arena.free(g->row_ptr);
         c->arena.free(g->col_idx);
         c->arena.free(g->orig);
         c->arena.free(d_new);
         c->arena.free(d_src);
+        c->arena.free(d_old_rp);
         return fail(CC_ERR_BUDGET, "graph does not fit the HBM budget");
     }
     CC_CUDA(cudaMemcpyAsync(g->row_ptr, g->h_row_ptr.data(), sizeof(int64_t) * (g->n_act + 1),
@@ -120,13 +130,20 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
             CC_CUDA(cudaMemcpyAsync(d_src, col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
             src = d_src;
         }
-        launch_remap(st, nnz, src, d_new, g->col_idx);
+        if (by_degree) {
+            CC_CUDA(cudaMemcpyAsync(d_old_rp, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+            launch_permute_lists(st, g->n_act, n, g->orig, d_old_rp, g->row_ptr, src, d_new, g->col_idx);
+        } else {
+            // input order: isolated vertices hold no edges, so list offsets are unchanged
+            launch_remap(st, nnz, n, src, d_new, g->col_idx);
+        }
         c->launches++;
     }
     CC_CUDA(cudaGetLastError());
     CC_CUDA(cudaStreamSynchronize(st));
     c->arena.free(d_new);
     c->arena.free(d_src);
+    c->arena.free(d_old_rp);
     int64_t id = c->next_id++;
     c->graphs[id] = std::move(g);
     *out = id;

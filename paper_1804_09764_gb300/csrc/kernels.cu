@@ -744,9 +744,25 @@ __global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, i
         if (s < Ch) {
             const uint64_t *ar = act + vb * Cas * L;
             const uint64_t *pr = agg + vb * Cps * L;
-            for (int64_t q = 0; q < npairs; q++) {
-                const uint32_t pq = __ldg(pairs + q * Ch + s);
-                wmac(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), wload<L, L>(pr + (pq >> 16) * L));
+            // in groups of G: split entries, then both operands, then the multiply-adds
+            constexpr int G = L <= 1 ? 4 : 2;
+            for (int64_t q0 = 0; q0 < npairs; q0 += G) {
+                uint32_t pq[G];
+#pragma unroll
+                for (int j = 0; j < G; j++) pq[j] = q0 + j < npairs ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
+                Wide<L> x[G], y[G];
+#pragma unroll
+                for (int j = 0; j < G; j++) {
+                    if (q0 + j < npairs) {
+                        x[j] = wload<L, L>(ar + (pq[j] & 0xFFFFu) * L);
+                        y[j] = wload<L, L>(pr + (pq[j] >> 16) * L);
+                    } else {
+                        wzero(x[j]);
+                        wzero(y[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < G; j++) wmac(acc, x[j], y[j]);
             }
         }
         wstore(out + i * L, acc);
@@ -821,11 +837,28 @@ __global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Ch
         if (s < Ch) {
             const uint64_t *ar = act + vb * Cas * L;
             const uint32_t *hr = hist + vb * k;
-#pragma unroll 4
-            for (int q = 0; q < h; q++) {
-                const uint32_t pq = __ldg(pairs + q * Ch + s);
-                const uint32_t hc = hr[pq >> 16];
-                if (hc) wmac_small(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), hc);
+            // in groups of G: the split entries, then the act values, then the
+            // multiply-adds, so the loads of a group are independent of each other
+            constexpr int G = L <= 1 ? 8 : 4;
+            for (int q0 = 0; q0 < h; q0 += G) {
+                uint32_t pq[G];
+#pragma unroll
+                for (int j = 0; j < G; j++) pq[j] = q0 + j < h ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
+                Wide<L> a[G];
+                uint32_t hc[G];
+#pragma unroll
+                for (int j = 0; j < G; j++) {
+                    if (q0 + j < h) {
+                        a[j] = wload<L, L>(ar + (pq[j] & 0xFFFFu) * L);
+                        hc[j] = hr[pq[j] >> 16];
+                    } else {
+                        wzero(a[j]);
+                        hc[j] = 0;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < G; j++)
+                    if (hc[j]) wmac_small(acc, a[j], hc[j]);
             }
         }
         wstore(out + i * L, acc);
@@ -942,11 +975,32 @@ __global__ void max_sum_kernel(int64_t n, const double *__restrict__ x, double *
     }
 }
 
-__global__ void remap_kernel(int64_t nnz, const int32_t *__restrict__ src, const int32_t *__restrict__ new_id,
-                             int32_t *__restrict__ dst)
+__global__ void remap_kernel(int64_t nnz, int64_t n, const int32_t *__restrict__ src,
+                             const int32_t *__restrict__ new_id, int32_t *__restrict__ dst)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < nnz) dst[i] = new_id[src[i]];
+    if (i < nnz) {
+        const int32_t u = src[i];
+        dst[i] = (u >= 0 && u < n) ? new_id[u] : 0;  // ids outside [0, n) only without CC_VALIDATE
+    }
+}
+
+// warp per new vertex: copies its neighbour list from the input CSR to the
+// relabelled CSR, mapping every neighbour id through new_id
+__global__ void permute_lists_kernel(int64_t n_act, int64_t n, const int64_t *__restrict__ orig,
+                                     const int64_t *__restrict__ old_rp, const int64_t *__restrict__ new_rp,
+                                     const int32_t *__restrict__ src, const int32_t *__restrict__ new_id,
+                                     int32_t *__restrict__ dst)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nv = blockIdx.x * (int64_t)kWarps + warp;
+    if (nv >= n_act) return;
+    const int64_t ov = orig[nv];
+    const int64_t a = old_rp[ov], len = old_rp[ov + 1] - a, b = new_rp[nv];
+    for (int64_t i = lane; i < len; i += 32) {
+        const int32_t u = src[a + i];
+        dst[b + i] = (u >= 0 && u < n) ? new_id[u] : 0;  // ids outside [0, n) only without CC_VALIDATE
+    }
 }
 
 inline unsigned grid_for(int64_t items, int per_cta) { return (unsigned)((items + per_cta - 1) / per_cta); }
@@ -1324,10 +1378,18 @@ void launch_max_sum(cudaStream_t st, int64_t n, const double *x, double *out)
     max_sum_kernel<<<grid_stride_ctas(n, 256), 256, 0, st>>>(n, x, out);
 }
 
-void launch_remap(cudaStream_t st, int64_t nnz, const int32_t *src, const int32_t *new_id, int32_t *dst)
+void launch_permute_lists(cudaStream_t st, int64_t n_act, int64_t n, const int64_t *orig, const int64_t *old_rp,
+                          const int64_t *new_rp, const int32_t *src, const int32_t *new_id, int32_t *dst)
+{
+    if (n_act == 0) return;
+    permute_lists_kernel<<<grid_for(n_act, kWarps), kWarps * 32, 0, st>>>(n_act, n, orig, old_rp, new_rp, src,
+                                                                           new_id, dst);
+}
+
+void launch_remap(cudaStream_t st, int64_t nnz, int64_t n, const int32_t *src, const int32_t *new_id, int32_t *dst)
 {
     if (nnz == 0) return;
-    remap_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, src, new_id, dst);
+    remap_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, n, src, new_id, dst);
 }
 
 }  // namespace cc

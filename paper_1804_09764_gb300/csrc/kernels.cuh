@@ -121,8 +121,12 @@ void launch_fill_double(cudaStream_t st, int64_t n, double v, double *x);
 // out[0] = max, out[1] = sum (out must be zeroed)
 void launch_max_sum(cudaStream_t st, int64_t n, const double *x, double *out);
 
+// relabelled CSR: list of new vertex nv = list of orig[nv] in the input CSR,
+// neighbour ids mapped through new_id
+void launch_permute_lists(cudaStream_t st, int64_t n_act, int64_t n, const int64_t *orig, const int64_t *old_rp,
+                          const int64_t *new_rp, const int32_t *src, const int32_t *new_id, int32_t *dst);
 // col_idx remap for the compact numbering: dst[e] = new_id[src[e]]
-void launch_remap(cudaStream_t st, int64_t nnz, const int32_t *src, const int32_t *new_id, int32_t *dst);
+void launch_remap(cudaStream_t st, int64_t nnz, int64_t n, const int32_t *src, const int32_t *new_id, int32_t *dst);
 
 int64_t reduce_scratch_ctas();
 

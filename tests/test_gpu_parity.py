@@ -308,3 +308,18 @@ def test_fused_and_unfused_gather_select(fused):
     res = c.count(gid, tid, seed=17, n_iter=3, want_maps=True)
     assert res["maps"] == maps
     c.close()
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_vertex_orders_give_identical_counts_and_samples(order):
+    g = gg.rmat_graph(10, seed=61)
+    k, e = gg.template_edges("caterpillar10")
+    _, pv = O.count_maps(g, k, e, 2, seed=6, j=0, per_vertex=True)
+    c = make_ctx(vertex_order=order, split_threshold=24)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 2)
+    sample = list(range(0, g.n, 5))
+    res = c.count(gid, tid, seed=6, n_iter=1, sample_vertices=sample, want_maps=True)
+    assert res["maps"][0] == sum(pv)
+    assert res["samples"][0] == [pv[v] for v in sample]
+    c.close()
