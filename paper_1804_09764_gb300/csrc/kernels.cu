@@ -837,28 +837,11 @@ __global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Ch
         if (s < Ch) {
             const uint64_t *ar = act + vb * Cas * L;
             const uint32_t *hr = hist + vb * k;
-            // in groups of G: the split entries, then the act values, then the
-            // multiply-adds, so the loads of a group are independent of each other
-            constexpr int G = L <= 1 ? 8 : 4;
-            for (int q0 = 0; q0 < h; q0 += G) {
-                uint32_t pq[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) pq[j] = q0 + j < h ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
-                Wide<L> a[G];
-                uint32_t hc[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) {
-                    if (q0 + j < h) {
-                        a[j] = wload<L, L>(ar + (pq[j] & 0xFFFFu) * L);
-                        hc[j] = hr[pq[j] >> 16];
-                    } else {
-                        wzero(a[j]);
-                        hc[j] = 0;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < G; j++)
-                    if (hc[j]) wmac_small(acc, a[j], hc[j]);
+#pragma unroll 4
+            for (int q = 0; q < h; q++) {
+                const uint32_t pq = __ldg(pairs + q * Ch + s);
+                const uint32_t hc = hr[pq >> 16];
+                if (hc) wmac_small(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), hc);
             }
         }
         wstore(out + i * L, acc);
