@@ -459,7 +459,8 @@ def main():
     line = {
         "metric": "edge_colourset_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64/u128/u192",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64" if info["limbs_root"] == 1 else f"u64..u{64 * info['limbs_root']}",
         "data": "synthetic",
         "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "n_active": info["n_active"],
                    "template": wl["template"], "k": k, "root": info["root"], "colourings_per_step": n_iter,

@@ -495,18 +495,97 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
             const uint64_t *cur = nullptr;
             int64_t cur_stride = k;
             uint64_t *root_rows = (uint64_t *)W(p->off_root);
-            for (size_t si = 0; si < C.steps.size(); si++) {
-                const Step &s = C.steps[si];
+            // output row block and stride of step si of this chain
+            auto step_out = [&](size_t si, int64_t *Chs_out) -> uint64_t * {
                 const bool last = si + 1 == C.steps.size();
-                const int64_t Ch = binom(k, s.h);
+                const int64_t Ch = binom(k, C.steps[si].h);
                 // root rows hold one column and are never gathered: no padding
                 const int64_t Chs = (last && C.is_root) ? 1 : col_stride(Ch);
-                uint64_t *out;
+                *Chs_out = Chs;
                 if (last)
-                    out = C.is_root ? root_rows
-                                    : (uint64_t *)W(p->off_table[ci]) + (uint64_t)v0 * B * Chs * L;
-                else
-                    out = (uint64_t *)W(p->off_act[si & 1]);
+                    return C.is_root ? root_rows : (uint64_t *)W(p->off_table[ci]) + (uint64_t)v0 * B * Chs * L;
+                return (uint64_t *)W(p->off_act[si & 1]);
+            };
+            // Chain fusion: a fused first step followed only by leaf (p = 1) steps
+            // runs as one kernel for light vertices; heavy vertices (a prefix of the
+            // block under degree ordering) take the task path and the p = 1 kernels.
+            size_t nleaf = 0;
+            if (c->opt.fused && c->opt.vertex_order == 0 && C.steps.size() >= 2 && C.steps[0].a == 1 &&
+                C.steps[0].src_chain >= 0 && !C.steps[1].reuse_agg && C.steps.size() - 1 <= 15) {
+                nleaf = C.steps.size() - 1;
+                for (size_t j = 1; j < C.steps.size(); j++)
+                    if (C.steps[j].src_chain >= 0) nleaf = 0;
+                // heavy vertices of the block must be its first rows
+                if (hv.h1 > hv.h0 && (sp.h_heavy_v[hv.h0] != v0 || sp.h_heavy_v[hv.h1 - 1] != v0 + (hv.h1 - hv.h0) - 1))
+                    nleaf = 0;
+            }
+            if (nleaf > 0) {
+                const Step &s = C.steps[0];
+                const int Ls = p->chain_L[s.src_chain];
+                const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
+                const int64_t R = (int64_t)B * Cps;
+                const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                uint64_t *agg = (uint64_t *)W(p->off_agg);
+                int64_t Chs0;
+                uint64_t *out0 = step_out(0, &Chs0);
+                const int64_t Ch0 = binom(k, s.h);
+                // Intermediate steps alternate between the two act buffers with their
+                // own row strides; inside one kernel a vertex's rows for step j + 2
+                // would then land on other vertices' step-j rows, so every light
+                // vertex gets one slot of the widest intermediate row instead.  The
+                // last step writes the chain's table (its own buffer, usual stride).
+                int64_t slot = 0;
+                for (size_t j = 0; j < nleaf; j++) slot = std::max(slot, col_stride(binom(k, C.steps[j].h)));
+                slot *= (int64_t)B * L;
+                auto vstride = [&](size_t j, int64_t cs) { return j == nleaf ? (int64_t)B * cs * L : slot; };
+                LeafChain lc{};
+                lc.n = (int)nleaf;
+                for (size_t j = 1; j <= nleaf; j++) {
+                    int64_t cs;
+                    lc.out[j - 1] = step_out(j, &cs);
+                    lc.h[j - 1] = C.steps[j].h;
+                    lc.Ch[j - 1] = binom(k, C.steps[j].h);
+                    lc.Chs[j - 1] = cs;
+                    lc.vs[j - 1] = vstride(j, cs);
+                    lc.pairs[j - 1] = p->d_pairs.at({C.steps[j].h, C.steps[j].a});
+                }
+                const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
+                double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Ch0 * 8.0 * L;
+                for (size_t j = 1; j <= nleaf; j++)
+                    bytes += (double)nv * B * (binom(k, C.steps[j].h) + binom(k, C.steps[j].a)) * 8.0 * L;
+                Ln.begin(K_FUSED);
+                // the chain kernel indexes colours and histograms by global vertex id
+                launch_gather_select_chain(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
+                                           Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, vstride(0, Chs0), lc, hist,
+                                           next_counter());
+                int nl = 1;
+                const int64_t nh = hv.h1 - hv.h0;
+                if (nh > 0) {
+                    uint64_t *part = (uint64_t *)W(p->off_partial);
+                    launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
+                                        next_counter(), 4);
+                    launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
+                    launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch0, Chs0, Cps, p->d_rm[s.h], col,
+                                        agg, out0);
+                    nl += 3;
+                    const uint64_t *prev = out0;
+                    int64_t prev_s = Chs0;
+                    for (int j = 0; j < lc.n; j++) {
+                        launch_combine_hist(st, L, nh, B, k, lc.Ch[j], lc.Chs[j], prev_s, lc.h[j], lc.pairs[j], prev,
+                                            hrow, lc.out[j]);
+                        prev = lc.out[j];
+                        prev_s = lc.Chs[j];
+                        nl++;
+                    }
+                }
+                Ln.end(nl, bytes);
+            }
+            for (size_t si = nleaf > 0 ? C.steps.size() : 0; si < C.steps.size(); si++) {
+                const Step &s = C.steps[si];
+                const int64_t Ch = binom(k, s.h);
+                int64_t Chs;
+                uint64_t *out = step_out(si, &Chs);
                 if (s.src_chain < 0) {
                     const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
                     if (s.a == 1) {

@@ -708,6 +708,90 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
     }
 }
 
+// Fused gather + a = 1 combine followed, in the same warp, by the chain's p = 1
+// steps for that vertex (see LeafChain).  The rows a warp writes are the rows
+// it reads next; __syncwarp orders them within the warp.
+template <int Ls, int Ld, int VPT, int NB>
+__global__ void __launch_bounds__(kWarps * 32)
+gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
+                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
+                           const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col, uint64_t *out,
+                           int64_t out_vs, LeafChain chain, const uint32_t *__restrict__ hist,
+                           unsigned long long *next)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t R = (int64_t)B * Cps;
+    while (true) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(next, 1ull);
+        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        if (v >= v1) return;
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select, p = 1 kernels
+        uint64_t *orow = out + (v - v0) * out_vs;
+        const uint8_t *cv = col + v * B;
+        for (int64_t i = lane; i < (int64_t)B * Chs; i += 32) {
+            const int64_t b = i / Chs, S = i - b * Chs;
+            if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
+                Wide<Ld> z;
+                wzero(z);
+                wstore(orow + i * Ld, z);
+            }
+        }
+        for (int64_t base = 0; base < R; base += 32 * VPT) {
+            Wide<Ld> acc[VPT];
+#pragma unroll
+            for (int q = 0; q < VPT; q++) wzero(acc[q]);
+            accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+#pragma unroll
+            for (int q = 0; q < VPT; q++) {
+                const int64_t c = base + q * 32 + lane;
+                if (c < R) {
+                    const int64_t b = c / Cps, T = c - b * Cps;
+                    if (T < Cp) {
+                        const uint32_t d = add_p[T * k + cv[b]];
+                        if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Ld, acc[q]);
+                    }
+                }
+            }
+        }
+        // the chain's p = 1 steps
+        const uint64_t *prev = orow;
+        int64_t prev_s = Chs;
+        const uint32_t *hr = hist + v * (int64_t)B * k;
+        for (int j = 0; j < chain.n; j++) {
+            __syncwarp();
+            const int64_t cj = chain.Ch[j], csj = chain.Chs[j];
+            const int hj = chain.h[j];
+            const uint32_t *pt = chain.pairs[j];
+            uint64_t *dst = chain.out[j] + (v - v0) * chain.vs[j];
+            for (int64_t i = lane; i < (int64_t)B * csj; i += 32) {
+                const int64_t b = i / csj, S = i - b * csj;
+                Wide<Ld> acc;
+                wzero(acc);
+                if (S < cj) {
+                    const uint64_t *ar = prev + b * prev_s * Ld;
+                    const uint32_t *hb = hr + b * k;
+                    for (int q = 0; q < hj; q++) {
+                        const uint32_t pq = __ldg(pt + q * cj + S);
+                        const uint32_t hc = hb[pq >> 16];
+                        if (hc) {
+                            Wide<Ld> a;
+#pragma unroll
+                            for (int l = 0; l < Ld; l++) a.w[l] = ar[(pq & 0xFFFFu) * Ld + l];
+                            wmac_small(acc, a, hc);
+                        }
+                    }
+                }
+                wstore(dst + i * Ld, acc);
+            }
+            prev = dst;
+            prev_s = csj;
+        }
+    }
+}
+
 template <int Ld>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_reduce_kernel(int64_t h0, int64_t h1, int64_t v0, int64_t t0, const int32_t *__restrict__ heavy_v,
@@ -1311,6 +1395,39 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
     CC_GS(3, 1); CC_GS(3, 2); CC_GS(3, 3); CC_GS(3, 4);
     CC_GS(4, 1); CC_GS(4, 2); CC_GS(4, 3); CC_GS(4, 4);
 #undef CC_GS
+}
+
+namespace {
+
+template <int Ls, int Ld>
+void gather_select_chain_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
+                           const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
+                           int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col,
+                           uint64_t *out, int64_t out_vs, const LeafChain &chain, const uint32_t *hist,
+                           unsigned long long *next)
+{
+    constexpr int VPT = Ld <= 2 ? 4 : 2;
+    auto kfn = nb == 4 ? gather_select_chain_kernel<Ls, Ld, VPT, 4> : gather_select_chain_kernel<Ls, Ld, VPT, 2>;
+    const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
+    kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
+                                   out_vs, chain, hist, next);
+}
+
+}  // namespace
+
+void launch_gather_select_chain(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                                const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
+                                int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
+                                const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
+                                const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb)
+{
+    if (v1 <= v0) return;
+#define CC_GC(a, b) if (Ls == a && Ld == b) return gather_select_chain_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, hist, next)
+    CC_GC(1, 1); CC_GC(1, 2); CC_GC(1, 3); CC_GC(1, 4);
+    CC_GC(2, 1); CC_GC(2, 2); CC_GC(2, 3); CC_GC(2, 4);
+    CC_GC(3, 1); CC_GC(3, 2); CC_GC(3, 3); CC_GC(3, 4);
+    CC_GC(4, 1); CC_GC(4, 2); CC_GC(4, 3); CC_GC(4, 4);
+#undef CC_GC
 }
 
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,

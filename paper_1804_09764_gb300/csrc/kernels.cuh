@@ -101,6 +101,26 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                           const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next,
                           int nb = 4);
+// Chain version: after the fused step the same warp runs the chain's following
+// p = 1 steps (leaf children) for the vertex, out_j[S] = sum over c in S of
+// out_{j-1}[S \ {c}] * hist[c].  The rows of vertex v for step j start at
+// out[j] + (v - v0) * vs[j] (vs in 64-bit words, >= B * Chs[j] * Ld): steps that
+// share a buffer give every vertex the same slot, so no warp writes into rows
+// another warp has yet to read.  col and hist are the whole-graph arrays
+// (indexed by global vertex id).
+struct LeafChain {
+    int n;                       // number of p = 1 steps after the fused step (<= 15)
+    int h[15];
+    int64_t Ch[15], Chs[15], vs[15];
+    const uint32_t *pairs[15];   // (h, h-1) split tables
+    uint64_t *out[15];
+};
+void launch_gather_select_chain(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+                                const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
+                                int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
+                                const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
+                                const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb = 4);
+
 // a = 1 combine for heavy vertices [h0, h1) of the heavy list (aggregates from the task path)
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,
                          int k, int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,

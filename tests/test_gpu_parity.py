@@ -310,6 +310,24 @@ def test_fused_and_unfused_gather_select(fused):
     c.close()
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_leaf_chain_after_fused_step(fused):
+    # broom: hub 0 with the path 1-2-3 and six leaves.  The hub's chain is one
+    # a = 1 step (the path) followed by six p = 1 steps whose rows widen and then
+    # narrow (C(10, h) for h = 4..10), run as one kernel per block when fused;
+    # heavy vertices (split 10), three vertex blocks and two colourings per pass.
+    g = gg.rmat_graph(11, seed=45)
+    k = 10
+    e = np.array([(0, 1), (1, 2), (2, 3)] + [(0, j) for j in range(4, 10)], dtype=np.int32)
+    maps = oracle_maps(g, k, e, 0, 19, range(3))
+    c = make_ctx(fused=fused, split_threshold=10, batch=2, block_vertices=600)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 0)
+    res = c.count(gid, tid, seed=19, n_iter=3, want_maps=True)
+    assert res["maps"] == maps
+    c.close()
+
+
 @pytest.mark.parametrize("order", [0, 1])
 def test_vertex_orders_give_identical_counts_and_samples(order):
     g = gg.rmat_graph(10, seed=61)
