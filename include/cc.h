@@ -88,7 +88,11 @@ typedef struct cc_options {
                                   fastest. */
     int32_t vertex_order;      /* 0 (default): active vertices numbered by decreasing degree
                                   (hub rows contiguous); 1: input order */
-    int32_t reserved[4];
+    int32_t col_chunks;        /* column segments per neighbour row in the persistent gathers
+                                  (segment-major work order, so hub rows' segments are reused
+                                  from L2): 0 (default) about 1.5 KiB per segment (at most
+                                  16), 1 whole rows */
+    int32_t reserved[3];
 } cc_options;
 
 void cc_default_options(cc_options *opt);
@@ -197,8 +201,15 @@ typedef struct cc_plan_info {
 
 cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out);
 
-/* Per-kernel CUDA-event statistics (opt.timing = 1); cumulative since reset. */
-#define CC_KERNEL_KINDS 8
+/* Per-kernel CUDA-event statistics (opt.timing = 1); cumulative since reset.
+ * Kinds, in order: colour; hist (colour histograms of N(v), the leaf gather);
+ * gather (table gather of vertices with at most split_threshold neighbours);
+ * combine (general Eq. 1 combine); reduce (root sum); fused (table gather +
+ * a = 1 combine, with the leaf steps that follow it in the chain, for those
+ * vertices); select (a = 1 combine); combine_hist (p = 1 combine); heavy
+ * (vertices with more neighbours: Algorithm 4 sub-list tasks, their partial-row
+ * sums and the combines that follow them in a fused step). */
+#define CC_KERNEL_KINDS 9
 typedef struct cc_kernel_stats {
     const char *name[CC_KERNEL_KINDS];
     int64_t launches[CC_KERNEL_KINDS];
@@ -291,6 +302,79 @@ typedef struct cc_serve_stats {
 } cc_serve_stats;
 
 cc_status cc_serve_stats_get(cc_ctx *ctx, cc_serve_stats *out);
+
+/* ------------------------------------------------- several templates at once */
+
+/*
+ * Counts of n_tmpl templates with the same k over the same colourings (the
+ * colourings of cc_count with args->seed, first_iter, n_iter).  The templates
+ * are planned one by one (their requested roots, or the planner's) and merged:
+ * a rooted subtree whose canonical form already occurs in an earlier template
+ * reuses that table, and the colouring and colour histograms are computed once
+ * per pass for all of them -- the shared sub-templates of graphlet-frequency
+ * counting (Section 2.1: each table depends only on the rooted subtree T_i and
+ * the colouring).  Results equal those of cc_count on each template.
+ *   counts, args->maps: [n_tmpl][n_iter][limbs_capacity]; res: [n_tmpl] (or NULL;
+ *   device_seconds and kernel_launches there are those of the shared passes).
+ *   args->n_sample must be 0.  The merged plan is not cached.
+ * Errors: as cc_count; CC_ERR_INVALID_ARG for n_tmpl < 1, different k, or
+ * sampled vertices.
+ */
+cc_status cc_count_multi(cc_ctx *ctx, cc_graph_id g, const cc_template_id *tmpls, int32_t n_tmpl,
+                         const cc_count_args *args, uint64_t *counts, int32_t limbs_capacity, cc_result *res);
+
+typedef struct cc_multi_info {
+    int32_t chains;                  /* tables (chains) of the merged plan */
+    int32_t chains_separate;         /* their sum over the templates planned alone */
+    double updates_per_colouring;    /* gathered edge x colour-set updates, merged */
+    double updates_per_colouring_separate;
+    uint64_t workspace_bytes;        /* merged plan, for n_iter colourings */
+    int32_t batch;
+    int32_t reserved;
+} cc_multi_info;
+
+/* Plans the merged count (as cc_count_multi with n_iter colourings) without
+ * running it. */
+cc_status cc_multi_plan_info_get(cc_ctx *ctx, cc_graph_id g, const cc_template_id *tmpls, int32_t n_tmpl,
+                                 int32_t n_iter, cc_multi_info *out);
+
+/* ------------------------------------------------- (epsilon, delta) driver */
+
+/*
+ * Algorithm 1's sample size, with the constants it leaves as O(.) fixed by the
+ * following argument.  With N copies of T and p = k!/k^k, the colourful count
+ * Y of one colouring satisfies 0 <= Y <= N and E[Y] = pN, so E[Y^2] <= N E[Y]
+ * and X = Y/p (Eq. 3) has Var X / (E X)^2 <= 1/p - 1.  The mean of
+ * s = ceil(4 (1/p - 1) / epsilon^2) colourings is then outside (1 +- epsilon) N
+ * with probability <= 1/4 (Chebyshev), and the median of
+ * t = ceil(8 ln(1/delta)) such means with probability <= exp(-t/8) <= delta
+ * (Hoeffding on the number of failed groups).
+ *   n_iter = s * t (at least 1 each), groups = t.  Host only, FP64.
+ * Errors: CC_ERR_K_RANGE (k outside 1..16); CC_ERR_INVALID_ARG (NULL outputs,
+ * epsilon <= 0, delta outside (0, 1), NaN); CC_ERR_CAPACITY (n_iter >= 2^62).
+ */
+cc_status cc_iterations_for(int32_t k, double epsilon, double delta, int64_t *n_iter, int32_t *groups);
+
+typedef struct cc_estimate_result {
+    int32_t k;
+    int32_t groups;           /* t */
+    int64_t n_iter;           /* colourings counted: groups * per_group */
+    int64_t per_group;        /* s */
+    double estimate;          /* median of the t group means of (k^k/k!) * copies_j */
+    double mean;              /* mean over all colourings */
+    double min_group_mean, max_group_mean;
+    double device_seconds, wall_seconds;
+} cc_estimate_result;
+
+/*
+ * Algorithm 1 end to end: colourings first_iter .. first_iter + n_iter - 1 of
+ * `seed` (n_iter, t from cc_iterations_for), counted exactly as cc_count does
+ * in chunks of at most 4096 colourings; colouring j belongs to group j / s.
+ * max_iter > 0 refuses (CC_ERR_CAPACITY, nothing run) when n_iter would exceed
+ * it.  Exact counts only (widths from the bound); errors as cc_count.
+ */
+cc_status cc_estimate(cc_ctx *ctx, cc_graph_id g, cc_template_id t, uint64_t seed, int64_t first_iter,
+                      double epsilon, double delta, int64_t max_iter, cc_estimate_result *out);
 
 /* ------------------------------------------------------------------ helpers */
 

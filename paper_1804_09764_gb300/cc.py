@@ -25,7 +25,7 @@ STATUS = {
     -13: "CC_ERR_INTERNAL",
 }
 CC_VALIDATE = 1
-KERNEL_KINDS = 8
+KERNEL_KINDS = 9
 
 # names every build must export (checked by the CPU test-suite)
 EXPORTED = [
@@ -34,6 +34,7 @@ EXPORTED = [
     "cc_count_ex", "cc_plan_info_get", "cc_kernel_stats_get", "cc_kernel_stats_reset", "cc_submit",
     "cc_poll", "cc_wait", "cc_cancel", "cc_serve_stats_get", "cc_template_cost",
     "cc_template_automorphisms", "cc_version", "cc_table_gather", "cc_table_gather_noalloc",
+    "cc_iterations_for", "cc_estimate", "cc_count_multi", "cc_multi_plan_info_get",
 ]
 
 
@@ -50,7 +51,7 @@ class cc_options(ctypes.Structure):
                 ("block_vertices", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("autotune", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("col_chunks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class cc_result(ctypes.Structure):
@@ -59,6 +60,19 @@ class cc_result(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("estimate", ctypes.c_double), ("median_of_means", ctypes.c_double),
                 ("device_seconds", ctypes.c_double), ("wall_seconds", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_int64)]
+
+
+class cc_multi_info(ctypes.Structure):
+    _fields_ = [("chains", ctypes.c_int32), ("chains_separate", ctypes.c_int32),
+                ("updates_per_colouring", ctypes.c_double), ("updates_per_colouring_separate", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_uint64), ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class cc_estimate_result(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("groups", ctypes.c_int32), ("n_iter", ctypes.c_int64),
+                ("per_group", ctypes.c_int64), ("estimate", ctypes.c_double), ("mean", ctypes.c_double),
+                ("min_group_mean", ctypes.c_double), ("max_group_mean", ctypes.c_double),
+                ("device_seconds", ctypes.c_double), ("wall_seconds", ctypes.c_double)]
 
 
 class cc_count_args(ctypes.Structure):
@@ -135,6 +149,10 @@ def load_library(path: str = LIB_PATH):
         "cc_version": (ctypes.c_char_p, []),
         "cc_table_gather": (I32, [P, I64, P, P, P, P, I64, I32, I32]),
         "cc_table_gather_noalloc": (I32, [I64, P, P, P, P, I64, I32, I32, P]),
+        "cc_iterations_for": (I32, [I32, ctypes.c_double, ctypes.c_double, P, P]),
+        "cc_estimate": (I32, [P, I64, I64, U64, I64, ctypes.c_double, ctypes.c_double, I64, P]),
+        "cc_count_multi": (I32, [P, I64, P, I32, P, P, I32, P]),
+        "cc_multi_plan_info_get": (I32, [P, I64, P, I32, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,6 +205,15 @@ def cc_template_automorphisms(k: int, edges) -> int:
     return a.value
 
 
+def cc_iterations_for(k: int, epsilon: float, delta: float) -> tuple[int, int]:
+    """(n_iter, groups) of Algorithm 1 for a (1 +- epsilon) estimate with
+    probability >= 1 - delta (host only)."""
+    lib = load_library()
+    n, t = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib.cc_iterations_for(k, float(epsilon), float(delta), ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
 def cc_table_gather_noalloc(row_ptr, col_idx, X, agg, values: int, limbs: int, split: int = 0,
                             stream: int = 0):
     """cc_table_gather_noalloc on torch device tensors (no context, no device
@@ -211,7 +238,7 @@ class Context:
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
                  fused: int = 1, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
-                 vertex_order: int = 0, stream=None):
+                 vertex_order: int = 0, col_chunks: int = 0, stream=None):
         import torch
 
         lib = load_library()
@@ -242,6 +269,7 @@ class Context:
         opt.timing = timing
         opt.gather_mode = gather_mode
         opt.vertex_order = vertex_order
+        opt.col_chunks = col_chunks
         torch.cuda.synchronize(device)
         h = ctypes.c_void_p()
         _check(lib.cc_create(ctypes.byref(h), ctypes.byref(opt)))
@@ -331,6 +359,39 @@ class Context:
             out["samples"] = [[limbs_to_int(r) for r in smaps[j]] for j in range(n_iter)]
         return out
 
+    def count_multi(self, gid: int, tids: Sequence[int], seed: int, n_iter: int, first_iter: int = 0,
+                    limbs_capacity: int = 4, width_bits: int = -1, mom_groups: int = 1,
+                    want_maps: bool = False) -> list:
+        """cc_count_multi: one result dict per template (as ``count``)."""
+        cap, nt = limbs_capacity, len(tids)
+        ids = np.ascontiguousarray(np.asarray(tids, dtype=np.int64))
+        counts = np.zeros((nt, max(n_iter, 1), cap), dtype=np.uint64)
+        maps = np.zeros((nt, max(n_iter, 1), cap), dtype=np.uint64) if want_maps else None
+        args = cc_count_args()
+        args.seed = seed & (2 ** 64 - 1)
+        args.first_iter = first_iter
+        args.n_iter = n_iter
+        args.mom_groups = mom_groups
+        args.width_bits = width_bits
+        if maps is not None:
+            args.maps = maps.ctypes.data
+        res = (cc_result * max(nt, 1))()
+        _check(self._lib.cc_count_multi(self._h, gid, _ptr(ids), nt, ctypes.byref(args), _ptr(counts), cap, res))
+        out = []
+        for r in range(nt):
+            d = {f: getattr(res[r], f) for f, _ in cc_result._fields_}
+            d["counts"] = [limbs_to_int(x) for x in counts[r, :n_iter]]
+            if maps is not None:
+                d["maps"] = [limbs_to_int(x) for x in maps[r, :n_iter]]
+            out.append(d)
+        return out
+
+    def multi_plan_info(self, gid: int, tids: Sequence[int], n_iter: int = 1) -> dict:
+        ids = np.ascontiguousarray(np.asarray(tids, dtype=np.int64))
+        info = cc_multi_info()
+        _check(self._lib.cc_multi_plan_info_get(self._h, gid, _ptr(ids), len(tids), n_iter, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in cc_multi_info._fields_}
+
     def plan_info(self, gid: int, tid: int) -> dict:
         info = cc_plan_info()
         _check(self._lib.cc_plan_info_get(self._h, gid, tid, ctypes.byref(info)))
@@ -345,6 +406,14 @@ class Context:
             out[nm] = dict(launches=s.launches[i], seconds=s.seconds[i], bytes=s.bytes[i])
         out["total_launches"] = s.total_launches
         return out
+
+    def estimate(self, gid: int, tid: int, seed: int, epsilon: float, delta: float, first_iter: int = 0,
+                 max_iter: int = 0) -> dict:
+        """cc_estimate: Algorithm 1 end to end (median of group means)."""
+        r = cc_estimate_result()
+        _check(self._lib.cc_estimate(self._h, gid, tid, seed & (2 ** 64 - 1), first_iter, float(epsilon),
+                                     float(delta), max_iter, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in cc_estimate_result._fields_}
 
     def kernel_stats_reset(self):
         _check(self._lib.cc_kernel_stats_reset(self._h))

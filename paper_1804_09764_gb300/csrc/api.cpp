@@ -1,5 +1,6 @@
 // api.cpp -- the extern "C" entry points declared in include/cc.h.
 #include <cstring>
+#include <vector>
 
 #include "runtime.h"
 
@@ -243,6 +244,48 @@ cc_status cc_count_ex(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_cou
                       args->n_sample > 0 ? args->sample_maps : nullptr, res);
 }
 
+cc_status cc_count_multi(cc_ctx *ctx, cc_graph_id g, const cc_template_id *tmpls, int32_t n_tmpl,
+                         const cc_count_args *args, uint64_t *counts, int32_t limbs_capacity, cc_result *res)
+{
+    if (!ctx || !args || !tmpls || n_tmpl < 1) return fail(CC_ERR_INVALID_ARG, "ctx, args or templates missing");
+    if (args->n_iter < 0 || limbs_capacity < 1) return fail(CC_ERR_INVALID_ARG, "n_iter < 0 or limbs_capacity < 1");
+    if (args->n_sample != 0) return fail(CC_ERR_INVALID_ARG, "sampled vertices need a single template");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    CountJob job;
+    job.seed = args->seed;
+    job.first_iter = args->first_iter;
+    job.n_iter = args->n_iter;
+    job.mom_groups = args->mom_groups > 0 ? args->mom_groups : 1;
+    job.width_bits = args->width_bits;
+    if (res) std::memset(res, 0, sizeof *res * n_tmpl);
+    return count_multi_sync(c, g, std::vector<int64_t>(tmpls, tmpls + n_tmpl), job, counts, limbs_capacity,
+                            args->maps, res);
+}
+
+cc_status cc_multi_plan_info_get(cc_ctx *ctx, cc_graph_id g, const cc_template_id *tmpls, int32_t n_tmpl,
+                                 int32_t n_iter, cc_multi_info *out)
+{
+    if (!ctx || !tmpls || n_tmpl < 1 || !out || n_iter < 1) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    std::unique_ptr<PlanInstance> p;
+    cc_status rc = make_plan_multi(c, g, std::vector<int64_t>(tmpls, tmpls + n_tmpl), n_iter,
+                                   c->opt.width_bits, c->stream, &p);
+    if (rc != CC_OK) return rc;
+    std::memset(out, 0, sizeof *out);
+    out->chains = (int32_t)p->tp.chains.size();
+    out->chains_separate = p->sep_chains;
+    out->updates_per_colouring = p->updates;
+    out->updates_per_colouring_separate = p->sep_updates;
+    out->workspace_bytes = p->ws_bytes;
+    out->batch = p->B;
+    free_plan(c, p.get());
+    return CC_OK;
+}
+
 cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out)
 {
     if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
@@ -283,7 +326,7 @@ cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out)
     if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
-    static const char *names[CC_KERNEL_KINDS] = {"colour", "hist", "gather", "combine", "reduce", "fused", "select", "combine_hist"};
+    static const char *names[CC_KERNEL_KINDS] = {"colour", "hist", "gather", "combine", "reduce", "fused", "select", "combine_hist", "heavy"};
     std::memset(out, 0, sizeof *out);
     for (int i = 0; i < CC_KERNEL_KINDS; i++) {
         out->name[i] = names[i];

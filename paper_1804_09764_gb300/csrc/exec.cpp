@@ -83,6 +83,10 @@ cc_status hom_bounds(Ctx *c, Graph *g, const TemplatePlan &tp, cudaStream_t st, 
     return CC_OK;
 }
 
+// consecutive vertices per work item of a column-segmented gather (fewer
+// claims on the work counter when every row is split into segments)
+static int vertex_group(int nch) { return nch > 1 ? 4 : 1; }
+
 int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(l2, 1000.0))); }
 
 struct Layout {
@@ -112,6 +116,11 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
         h.h1 = std::lower_bound(sp.h_heavy_v.begin(), sp.h_heavy_v.end(), (int32_t)b.second) - sp.h_heavy_v.begin();
         h.t0 = sp.h_heavy_tptr[h.h0];
         h.t1 = sp.h_heavy_tptr[h.h1];
+        h.edges = 0;
+        for (int64_t i = h.h0; i < h.h1; i++) {
+            const int32_t v = sp.h_heavy_v[i];
+            h.edges += g.h_row_ptr[v + 1] - g.h_row_ptr[v];
+        }
         Lo.max_tasks = std::max(Lo.max_tasks, h.t1 - h.t0);
         Lo.heavy.push_back(h);
     }
@@ -165,7 +174,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     Lo.off_partial = take((uint64_t)std::max<int64_t>(Lo.max_tasks, 1) * B * maxP * 8 * Lm);
     Lo.off_root = take((uint64_t)V * B * 8 * p.L_root);
     Lo.off_scratch = take((uint64_t)reduce_scratch_ctas() * B * 8 * p.L_root);
-    Lo.off_totals = take((uint64_t)B * 8 * p.L_root);
+    Lo.off_totals = take((uint64_t)p.n_slots * B * 8 * p.L_root);
     Lo.off_params = take(sizeof(ColourParams));
     Lo.off_err = take(256);
     Lo.off_ctr = take(kWorkCounters * 8);
@@ -175,22 +184,16 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
 
 }  // namespace
 
-cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
-                    std::unique_ptr<PlanInstance> *out)
+namespace {
+
+// The partition of one template against graph g: from its requested root, or
+// the planner's choice (least modelled time with the widths each root needs),
+// with every chain's integer width.
+cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, cudaStream_t st,
+                           TemplatePlan *tp_out, std::vector<int> *chain_L_out, int *L_root_out)
 {
-    auto git = c->graphs.find(gid);
-    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
-    auto tit = c->templates.find(tid);
-    if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
-    Graph *g = git->second.get();
-    Template *t = tit->second.get();
-    auto p = std::make_unique<PlanInstance>();
-    p->graph_id = gid;
-    p->tmpl_id = tid;
     std::string err;
     double avg = g->n_act ? (double)g->nnz / g->n_act : 1.0;
-    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
-        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
     // Integer widths of a partition: every chain at the smallest L with
     // max_v H(v) < 2^(64 L), capped at the root's L (which covers sum_v H).
     auto widths = [&](const TemplatePlan &tp, std::vector<int> *chain_L, int *L_root) -> cc_status {
@@ -237,9 +240,9 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
         return bytes / 6.0e12 + work / 3.0e11;
     };
     if (t->root_req >= 0 || t->k <= 2 || g->n_act == 0) {
-        int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &p->tp, &err);
+        int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &*tp_out, &err);
         if (rc) return fail(rc, err);
-        CC_TRY(widths(p->tp, &p->chain_L, &p->L_root));
+        CC_TRY(widths(*tp_out, chain_L_out, L_root_out));
     } else {
         // the planner's root: the least modelled time with the widths each root
         // needs.  The model at 64-bit widths is a lower bound, so roots are tried
@@ -264,12 +267,126 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
             const double m = model(tp, cl);
             if (m < best) {
                 best = m;
-                p->tp = tp;
-                p->chain_L = cl;
-                p->L_root = lr;
+                *tp_out = tp;
+                *chain_L_out = cl;
+                *L_root_out = lr;
             }
         }
     }
+    return CC_OK;
+}
+
+cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_bits, cudaStream_t st);
+
+}  // namespace
+
+cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
+                    std::unique_ptr<PlanInstance> *out)
+{
+    auto git = c->graphs.find(gid);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    auto tit = c->templates.find(tid);
+    if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
+    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
+        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
+    Graph *g = git->second.get();
+    auto p = std::make_unique<PlanInstance>();
+    p->graph_id = gid;
+    p->tmpl_id = tid;
+    CC_TRY(select_partition(c, g, tit->second.get(), width_bits, st, &p->tp, &p->chain_L, &p->L_root));
+    const int nc = (int)p->tp.chains.size();
+    p->n_slots = 1;
+    p->chain_slot.assign(nc, -1);
+    p->chain_slot[nc - 1] = 0;  // the root chain is last
+    p->tmpl_slot = {0};
+    p->tmpl_L = {p->L_root};
+    p->tmpl_root = {p->tp.root};
+    p->tmpl_aut = {p->tp.aut};
+    CC_TRY(finish_plan(c, g, p.get(), n_iter, width_bits, st));
+    *out = std::move(p);
+    return CC_OK;
+}
+
+cc_status make_plan_multi(Ctx *c, int64_t gid, const std::vector<int64_t> &tids, int n_iter, int width_bits,
+                          cudaStream_t st, std::unique_ptr<PlanInstance> *out)
+{
+    auto git = c->graphs.find(gid);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    if (tids.empty()) return fail(CC_ERR_INVALID_ARG, "no templates");
+    if (width_bits != 0 && width_bits != 64 && width_bits != 128 && width_bits != 192 && width_bits != 256)
+        return fail(CC_ERR_INVALID_ARG, "width_bits must be 0, 64, 128, 192 or 256");
+    Graph *g = git->second.get();
+    auto p = std::make_unique<PlanInstance>();
+    p->graph_id = gid;
+    p->tmpl_id = -1;
+    TemplatePlan &M = p->tp;
+    std::map<std::string, int> by_canon;  // rooted canonical form -> merged chain
+    std::vector<int> Ls;
+    p->n_slots = 0;
+    p->L_root = 1;
+    for (int64_t tid : tids) {
+        auto tit = c->templates.find(tid);
+        if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
+        const Template *t = tit->second.get();
+        if (M.k == 0) M.k = t->k;
+        if (t->k != M.k) return fail(CC_ERR_INVALID_ARG, "templates of one count must have the same k");
+        TemplatePlan tp;
+        std::vector<int> cl;
+        int lr = 1;
+        CC_TRY(select_partition(c, g, t, width_bits, st, &tp, &cl, &lr));
+        p->sep_chains += (int)tp.chains.size();
+        // chains in post-order; a chain whose rooted subtree is already planned
+        // reuses that table (the table depends only on the rooted subtree)
+        std::vector<int> map(tp.chains.size());
+        for (size_t i = 0; i < tp.chains.size(); i++) {
+            ChainPlan C = tp.chains[i];
+            for (auto &st_ : C.steps)
+                if (st_.src_chain >= 0 && !st_.reuse_agg)
+                    p->sep_updates += (double)g->nnz * (double)binom(M.k, st_.p);
+            auto it = by_canon.find(C.canon);
+            if (it != by_canon.end()) {
+                map[i] = it->second;
+                Ls[it->second] = std::max(Ls[it->second], cl[i]);
+                continue;
+            }
+            for (auto &st_ : C.steps)
+                if (st_.src_chain >= 0) st_.src_chain = map[st_.src_chain];
+            C.last_consumer = -1;
+            map[i] = (int)M.chains.size();
+            by_canon[C.canon] = map[i];
+            M.chains.push_back(C);
+            Ls.push_back(cl[i]);
+            p->chain_slot.push_back(C.is_root ? p->n_slots++ : -1);
+        }
+        p->tmpl_slot.push_back(p->chain_slot[map.back()]);
+        p->tmpl_L.push_back(lr);
+        p->tmpl_root.push_back(tp.root);
+        p->tmpl_aut.push_back(tp.aut);
+        p->L_root = std::max(p->L_root, lr);
+        M.table4_memory += tp.table4_memory;
+        M.table4_computation += tp.table4_computation;
+        M.pairs_per_vertex += tp.pairs_per_vertex;
+    }
+    M.root = p->tmpl_root[0];
+    M.aut = 1;
+    for (size_t ci = 0; ci < M.chains.size(); ci++)
+        for (auto &st_ : M.chains[ci].steps)
+            if (st_.src_chain >= 0) M.chains[st_.src_chain].last_consumer = (int)ci;
+    // every root chain at the widest root width; template r keeps its low tmpl_L[r] limbs
+    for (size_t ci = 0; ci < M.chains.size(); ci++)
+        if (M.chains[ci].is_root) Ls[ci] = p->L_root;
+    p->chain_L = Ls;
+    CC_TRY(finish_plan(c, g, p.get(), n_iter, width_bits, st));
+    *out = std::move(p);
+    return CC_OK;
+}
+
+namespace {
+
+// batch and block sizing under the budget, workspace layout, device constant
+// tables and the analytic per-colouring figures of a selected partition
+cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_bits, cudaStream_t st)
+{
     const TemplatePlan &tp = p->tp;
     const int k = tp.k;
     const int nc = (int)tp.chains.size();
@@ -303,8 +420,8 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     }
     if (!found) return fail(CC_ERR_BUDGET, "plan does not fit the HBM budget (largest free block " +
                                                std::to_string(room >> 20) + " MiB)");
-    {
-        auto tm = c->tuned_modes.find(std::make_tuple(gid, tid, p->B));
+    if (p->tmpl_id >= 0) {
+        auto tm = c->tuned_modes.find(std::make_tuple(p->graph_id, p->tmpl_id, p->B));
         if (tm != c->tuned_modes.end()) {
             p->site_mode = tm->second;
             p->tuned = true;
@@ -389,9 +506,10 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     for (auto &C : tp.chains)
         for (auto &s : C.steps) any_leaf |= s.src_chain < 0;
     if (any_leaf) p->alg_bytes += nnz + (4.0 * nnz + 8.0 * (na + 1)) / p->B;  // colour bytes + CSR
-    *out = std::move(p);
     return CC_OK;
 }
+
+}  // namespace
 
 void free_plan(Ctx *c, PlanInstance *p)
 {
@@ -468,7 +586,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     Launcher Ln(c, st);
     auto W = [&](uint64_t off) { return ws + off; };
     uint64_t *totals = (uint64_t *)W(p->off_totals);
-    CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)B * 8 * p->L_root, st));
+    CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)p->n_slots * B * 8 * p->L_root, st));
     uint8_t *col = (uint8_t *)W(p->off_col);
     unsigned long long *ctr = (unsigned long long *)W(p->off_ctr);
     int ctr_used = 0;
@@ -550,25 +668,42 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     lc.pairs[j - 1] = p->d_pairs.at({C.steps[j].h, C.steps[j].a});
                 }
                 const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
-                double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
-                double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Ch0 * 8.0 * L;
-                for (size_t j = 1; j <= nleaf; j++)
-                    bytes += (double)nv * B * (binom(k, C.steps[j].h) + binom(k, C.steps[j].a)) * 8.0 * L;
-                Ln.begin(K_FUSED);
-                // the chain kernel indexes colours and histograms by global vertex id
-                launch_gather_select_chain(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
-                                           Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, vstride(0, Chs0), lc, hist,
-                                           next_counter());
-                int nl = 1;
                 const int64_t nh = hv.h1 - hv.h0;
+                // algorithmic bytes of the chain for `nvert` vertices with `edges` list entries:
+                // neighbour rows + ids + row pointers + the step rows written, and per
+                // leaf step the previous row and the colour histogram read
+                auto chain_bytes = [&](double edges, double nvert) {
+                    double b = edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Ch0 * 8.0 * L;
+                    for (size_t j = 1; j <= nleaf; j++)
+                        b += nvert * B * ((binom(k, C.steps[j].h) + binom(k, C.steps[j].a)) * 8.0 * L + 4.0 * k);
+                    return b;
+                };
+                const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                const int nch = column_segments(R, Ls, c->opt.col_chunks);
+                Ln.begin(K_FUSED);
+                if (nch == 1) {
+                    // one kernel; it indexes colours and histograms by global vertex id
+                    launch_gather_select_chain(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
+                                               Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, vstride(0, Chs0), lc,
+                                               hist, next_counter());
+                } else {
+                    // column-segmented gather + select into the slots, then the leaf steps
+                    launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
+                                         Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, next_counter(), 4, nch,
+                                         vertex_group(nch), vstride(0, Chs0));
+                    launch_leaf_chain(st, L, v0, v1, p->split, g->row_ptr, B, k, out0, vstride(0, Chs0), Chs0, lc, hist,
+                                      next_counter());
+                }
+                Ln.end(nch == 1 ? 1 : 2, chain_bytes(e_blk - (double)hv.edges, (double)(nv - nh)));
                 if (nh > 0) {
+                    // heavy vertices (Algorithm 4): tasks, partial-row sums, select, leaf steps
+                    Ln.begin(K_HEAVY);
                     uint64_t *part = (uint64_t *)W(p->off_partial);
                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                        next_counter(), 4);
+                                        next_counter(), 4, column_segments(R, Ls, c->opt.col_chunks));
                     launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                     launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch0, Chs0, Cps, p->d_rm[s.h], col,
                                         agg, out0);
-                    nl += 3;
                     const uint64_t *prev = out0;
                     int64_t prev_s = Chs0;
                     for (int j = 0; j < lc.n; j++) {
@@ -576,10 +711,9 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                             hrow, lc.out[j]);
                         prev = lc.out[j];
                         prev_s = lc.Chs[j];
-                        nl++;
                     }
+                    Ln.end(3 + lc.n, chain_bytes((double)hv.edges, (double)nh));
                 }
-                Ln.end(nl, bytes);
             }
             for (size_t si = nleaf > 0 ? C.steps.size() : 0; si < C.steps.size(); si++) {
                 const Step &s = C.steps[si];
@@ -606,15 +740,21 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const int64_t R = (int64_t)B * Cps;
                     const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
-                    double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
-                    double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Ch * 8.0 * L;
+                    // algorithmic bytes: neighbour rows + ids + row pointers + output rows
+                    auto sel_bytes = [&](double edges, double nvert) {
+                        return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Ch * 8.0 * L;
+                    };
+                    const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                    const double light_bytes = sel_bytes(e_blk - (double)hv.edges, (double)(nv - (hv.h1 - hv.h0)));
                     Ln.begin(K_FUSED);
                     const auto site = std::make_pair((int)ci, (int)si);
+                    const int nch = column_segments(R, Ls, c->opt.col_chunks);
                     auto fused_run = [&](int nb) {
                         launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch,
-                                             Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(), nb);
+                                             Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(), nb, nch,
+                                             vertex_group(nch));
                     };
-                    int nl = 1, nb_tasks = 2;
+                    int nl = 0, nb_tasks = 2;
                     if (tune) {
                         for (int nb : {2, 4}) {  // the default (4) last
                             PlanInstance::Trial tr{(int)ci, (int)si, nb, nullptr, nullptr};
@@ -624,22 +764,26 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                             fused_run(nb);
                             cudaEventRecord(tr.b, st);
                             p->trials.push_back(tr);
+                            nl++;
                         }
                     } else {
                         auto it = p->site_mode.find(site);
                         nb_tasks = (it != p->site_mode.end() && it->second == 2) ? 2 : 4;
                         fused_run(nb_tasks);
+                        nl = 1;
                     }
+                    Ln.end(nl, nl * light_bytes);
                     if (hv.t1 > hv.t0) {
+                        // heavy vertices (Algorithm 4): tasks, partial-row sums, select
+                        Ln.begin(K_HEAVY);
                         uint64_t *part = (uint64_t *)W(p->off_partial);
                         launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                            next_counter(), nb_tasks);
+                                            next_counter(), nb_tasks, column_segments(R, Ls, c->opt.col_chunks));
                         launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                         launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
                                             agg, out);
-                        nl += 3;
+                        Ln.end(3, sel_bytes((double)hv.edges, (double)(hv.h1 - hv.h0)));
                     }
-                    Ln.end(nl, bytes);
                 } else {
                     const int Ls = p->chain_L[s.src_chain];
                     const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
@@ -648,14 +792,20 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
                     if (!s.reuse_agg) {
                         // algorithmic bytes of this gather: neighbour rows + CSR + aggregate write
-                        double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
-                        double bytes = e_blk * B * Cp * 8.0 * Ls + e_blk * 4 + nv * 8.0 + (double)nv * B * Cp * 8.0 * L;
-                        Ln.begin(K_GATHER);
+                        auto g_bytes = [&](double edges, double nvert) {
+                            return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Cp * 8.0 * L;
+                        };
+                        const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
+                        const int64_t nh = hv.h1 - hv.h0;
+                        const double light_bytes = g_bytes(e_blk - (double)hv.edges, (double)(nv - nh));
+                        const double heavy_bytes = g_bytes((double)hv.edges, (double)nh);
                         int *err = (int *)W(p->off_err);
+                        // light vertices timed as "gather", heavy ones (Algorithm 4 tasks) as "heavy"
                         auto run_gather = [&](int gm) {
                             const bool bulk = gm == 0 && bulk_gather_ok(Ls, R);
                             const bool group = gm == 3 && vec_gather_ok(Ls, R);
                             const bool vec = !bulk && !group && (gm == 0 || gm == 2) && vec_gather_ok(Ls, R);
+                            Ln.begin(K_GATHER);
                             if (bulk)
                                 launch_gather_light_bulk(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, g->nnz,
                                                          X, R, agg, err);
@@ -666,9 +816,12 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 launch_gather_light_vec(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
                             else
                                 launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
-                                                    gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4);
-                            int n = 1;
+                                                    gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
+                                                    column_segments(R, Ls, c->opt.col_chunks),
+                                                    vertex_group(column_segments(R, Ls, c->opt.col_chunks)));
+                            Ln.end(1, light_bytes);
                             if (hv.t1 > hv.t0) {
+                                Ln.begin(K_HEAVY);
                                 uint64_t *part = (uint64_t *)W(p->off_partial);
                                 if (bulk)
                                     launch_gather_tasks_bulk(st, Ls, L, hv.t0, hv.t1, g->col_idx, g->nnz, sp.task_e, X,
@@ -680,14 +833,13 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                     launch_gather_tasks_vec(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
                                 else
                                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
-                                                        gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4);
+                                                        gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
+                                                        column_segments(R, Ls, c->opt.col_chunks));
                                 launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
-                                n += 2;
+                                Ln.end(2, heavy_bytes);
                             }
-                            return n;
                         };
-                        int nl = 0;
                         const auto site = std::make_pair((int)ci, (int)si);
                         if (tune) {
                             // every variant computes the same sums; the last one run leaves agg
@@ -698,15 +850,14 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 cudaEventCreate(&tr.a);
                                 cudaEventCreate(&tr.b);
                                 cudaEventRecord(tr.a, st);
-                                nl += run_gather(gm);
+                                run_gather(gm);
                                 cudaEventRecord(tr.b, st);
                                 p->trials.push_back(tr);
                             }
                         } else {
                             auto it = p->site_mode.find(site);
-                            nl += run_gather(it != p->site_mode.end() ? it->second : c->opt.gather_mode);
+                            run_gather(it != p->site_mode.end() ? it->second : c->opt.gather_mode);
                         }
-                        Ln.end(nl, bytes);
                     }
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
@@ -725,7 +876,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
             if (C.is_root) {
                 Ln.begin(K_REDUCE);
                 launch_root_reduce(st, p->L_root, nv, B, root_rows, (uint64_t *)W(p->off_scratch),
-                                   reduce_scratch_ctas(), totals);
+                                   reduce_scratch_ctas(), totals + (size_t)p->chain_slot[ci] * B * p->L_root);
                 int nl = 2;
                 if (n_samples > 0) {
                     launch_sample_extract(st, p->L_root, n_samples, d_samples, v0, v1, B, root_rows, d_samples_out);
@@ -794,7 +945,7 @@ static cc_status finish_tuning(Ctx *c, PlanInstance *p, cudaStream_t st)
         }
     }
     p->tuned = true;
-    c->tuned_modes[std::make_tuple(p->graph_id, p->tmpl_id, p->B)] = p->site_mode;
+    if (p->tmpl_id >= 0) c->tuned_modes[std::make_tuple(p->graph_id, p->tmpl_id, p->B)] = p->site_mode;
     return CC_OK;
 }
 
@@ -819,8 +970,8 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
             CC_TRY(launch_pass(c, p, ws, st, d_samples, n_samples, d_samples_out, tune));
             if (tune) CC_TRY(finish_tuning(c, p, st));
         }
-        CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * B * p->L_root, ws + p->off_totals,
-                                (size_t)B * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
+        CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * p->n_slots * B * p->L_root, ws + p->off_totals,
+                                (size_t)p->n_slots * B * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
         if (n_samples > 0)
             CC_CUDA(cudaMemcpyAsync(host_samples + (size_t)ps * B * n_samples * p->L_root, d_samples_out,
                                     (size_t)B * n_samples * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
@@ -857,10 +1008,11 @@ double to_double(const uint64_t *x, int L)
 
 cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
                         const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
-                        uint64_t *sample_out, cc_result *res)
+                        uint64_t *sample_out, cc_result *res, int tr)
 {
     (void)c;
-    const int k = p->tp.k, L = p->L_root, B = p->B;
+    // totals rows hold L_root limbs; this template's total needs its low L limbs
+    const int k = p->tp.k, Lst = p->L_root, L = p->tmpl_L[tr], B = p->B, slot = p->tmpl_slot[tr];
     const int n_iter = job.n_iter;
     const int64_t ns = (int64_t)job.sample_vertices.size();
     cc_result r;
@@ -869,8 +1021,8 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
     r.limbs = L;
     r.exact = p->exact ? 1 : 0;
     r.n_iter = n_iter;
-    r.aut = p->tp.aut;
-    r.root = p->tp.root;
+    r.aut = p->tmpl_aut[tr];
+    r.root = p->tmpl_root[tr];
     r.batch = B;
     r.workspace_bytes = p->ws_bytes;
     if (cap < L) {
@@ -883,11 +1035,11 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
     std::vector<uint64_t> q(L);
     for (int j = 0; j < n_iter; j++) {
         const int ps = j / B, b = j % B;
-        const uint64_t *m = totals + ((size_t)ps * B + b) * L;
+        const uint64_t *m = totals + (((size_t)ps * p->n_slots + slot) * B + b) * Lst;
         if (maps)
             for (int l = 0; l < cap; l++) maps[(size_t)j * cap + l] = l < L ? m[l] : 0;
         if (p->exact) {
-            uint64_t rem = divmod_small(m, L, (uint64_t)p->tp.aut, q.data());
+            uint64_t rem = divmod_small(m, L, (uint64_t)p->tmpl_aut[tr], q.data());
             if (rem) return fail(CC_ERR_INTERNAL, "labelled map count not divisible by |Aut(T)|");
             for (int l = 0; l < cap; l++) counts[(size_t)j * cap + l] = l < L ? q[l] : 0;
             est[j] = to_double(q.data(), L) * (kk / kf);
@@ -901,7 +1053,7 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
                 int64_t cv = (ov >= 0 && ov < g->n) ? g->h_new_id[ov] : -1;
                 for (int l = 0; l < cap; l++) dst[l] = 0;
                 if (cv >= 0 && samples) {
-                    const uint64_t *src = samples + (((size_t)ps * B + b) * ns + s) * L;
+                    const uint64_t *src = samples + (((size_t)ps * B + b) * ns + s) * Lst;
                     for (int l = 0; l < L; l++) dst[l] = src[l];
                 }
             }
@@ -1045,7 +1197,7 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
         CC_CUDA(cudaMemsetAsync(cl.dso, 0, (size_t)8 * ns * B * p->L_root, st));
     }
     CC_CUDA(cudaMallocHost(&cl.hp, sizeof(ColourParams) * npass));
-    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root));
+    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root * p->n_slots));
     if (ns > 0) CC_CUDA(cudaMallocHost(&cl.hs, (size_t)8 * npass * B * ns * p->L_root));
     cudaEvent_t e0, e1;
     CC_CUDA(cudaEventCreate(&e0));
@@ -1074,6 +1226,96 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     if (res)
         res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     return rc;
+}
+
+cc_status count_multi_sync(Ctx *c, int64_t gid, const std::vector<int64_t> &tids, const CountJob &job,
+                           uint64_t *counts, int32_t cap, uint64_t *maps, cc_result *res)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    if (!counts) return fail(CC_ERR_INVALID_ARG, "counts is NULL");
+    if (job.n_iter < 0) return fail(CC_ERR_INVALID_ARG, "n_iter < 0");
+    if (tids.empty()) return fail(CC_ERR_INVALID_ARG, "no templates");
+    if (!job.sample_vertices.empty()) return fail(CC_ERR_INVALID_ARG, "sampled vertices need a single template");
+    auto git = c->graphs.find(gid);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    Graph *g = git->second.get();
+    std::vector<const Template *> ts;
+    for (int64_t tid : tids) {
+        auto tit = c->templates.find(tid);
+        if (tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown template");
+        ts.push_back(tit->second.get());
+        if (ts.back()->k != ts[0]->k) return fail(CC_ERR_INVALID_ARG, "templates of one count must have the same k");
+    }
+    const size_t nt = ts.size(), per = (size_t)job.n_iter * cap;
+    const int width = job.width_bits >= 0 ? job.width_bits : c->opt.width_bits;
+    if (ts[0]->k == 1 || g->n_act == 0 || job.n_iter == 0) {
+        for (size_t r = 0; r < nt; r++)
+            CC_TRY(trivial_counts(g, job, ts[r]->k, ts[r]->aut, counts + r * per, cap, maps ? maps + r * per : nullptr,
+                                  nullptr, res ? res + r : nullptr));
+        return CC_OK;
+    }
+    cudaStream_t st = c->stream;
+    std::unique_ptr<PlanInstance> p;
+    cc_status rc = make_plan_multi(c, gid, tids, job.n_iter, width, st, &p);
+    if (rc == CC_ERR_BUDGET && !c->plan_cache.empty()) {
+        evict_plans(c);
+        rc = make_plan_multi(c, gid, tids, job.n_iter, width, st, &p);
+    }
+    if (rc != CC_OK) return rc;
+    struct Cleanup {
+        Ctx *c;
+        PlanInstance *p;
+        char *ws = nullptr;
+        void *hp = nullptr, *ht = nullptr;
+        ~Cleanup()
+        {
+            cudaStreamSynchronize(c->stream);
+            c->arena.free(ws);
+            free_plan(c, p);
+            if (hp) cudaFreeHost(hp);
+            if (ht) cudaFreeHost(ht);
+        }
+    } cl{c, p.get()};
+    cl.ws = (char *)c->arena.alloc(p->ws_bytes);
+    if (!cl.ws && !c->plan_cache.empty()) {
+        evict_plans(c);
+        cl.ws = (char *)c->arena.alloc(p->ws_bytes);
+    }
+    if (!cl.ws) return fail(CC_ERR_BUDGET, "workspace does not fit the HBM budget");
+    const int B = p->B;
+    const int npass = (job.n_iter + B - 1) / B;
+    CC_CUDA(cudaMallocHost(&cl.hp, sizeof(ColourParams) * npass));
+    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root * p->n_slots));
+    cudaEvent_t e0, e1;
+    CC_CUDA(cudaEventCreate(&e0));
+    CC_CUDA(cudaEventCreate(&e1));
+    const int64_t l0 = c->launches.load();
+    CC_CUDA(cudaMemsetAsync(cl.ws + p->off_err, 0, 256, st));
+    CC_CUDA(cudaEventRecord(e0, st));
+    rc = run_passes(c, p.get(), cl.ws, job, 0, npass, st, (ColourParams *)cl.hp, (uint64_t *)cl.ht, nullptr, nullptr,
+                    0, nullptr, nullptr);
+    CC_CUDA(cudaEventRecord(e1, st));
+    CC_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CC_OK) return rc;
+    int kerr = 0;
+    CC_CUDA(cudaMemcpy(&kerr, cl.ws + p->off_err, sizeof kerr, cudaMemcpyDeviceToHost));
+    if (kerr) return fail(CC_ERR_TIMEOUT, "a gather kernel wait ran out of time (code " + std::to_string(kerr) + ")");
+    for (size_t r = 0; r < nt; r++) {
+        cc_result *rr = res ? res + r : nullptr;
+        if (rr) {
+            std::memset(rr, 0, sizeof *rr);
+            rr->device_seconds = ms * 1e-3;  // the shared passes
+            rr->kernel_launches = c->launches.load() - l0;
+        }
+        CC_TRY(finish_counts(c, p.get(), g, job, (const uint64_t *)cl.ht, nullptr, counts + r * per, cap,
+                             maps ? maps + r * per : nullptr, nullptr, rr, (int)r));
+        if (rr) rr->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return CC_OK;
 }
 
 void *arena_alloc(Ctx *c, uint64_t bytes)

@@ -33,16 +33,23 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 // next: zeroed device counter -> persistent grid whose warps pull items from it;
 //       nullptr -> one warp per item
 // nb: neighbour rows loaded before adding (2 or 4)
+// nch, G (with next): work items are (column segment, G consecutive vertices),
+// segment-major (see launch_gather_tasks)
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
                          int64_t R, uint64_t *agg, bool prefetch = false, unsigned long long *next = nullptr,
-                         int nb = 4);
+                         int nb = 4, int nch = 1, int G = 1);
 
 // tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
+// nch > 1 (with next): the row is split into nch column segments run
+// segment-major, so hub rows' segments are reused from L2 by the warps in flight
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
                          const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
                          int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr,
-                         int nb = 4);
+                         int nb = 4, int nch = 1);
+
+// column segments for rows of R values of Ls limbs: 0 = about 3 KiB per segment
+int column_segments(int64_t R, int Ls, int requested);
 
 // Vectorised warp versions (16-byte loads, several neighbours in flight) for
 // rows of 1- or 2-limb values; usable when vec_gather_ok(Ls, R).
@@ -100,7 +107,9 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
                           const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                           const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next,
-                          int nb = 4);
+                          int nb = 4, int nch = 1, int G = 1, int64_t out_vs = 0);
+// (nch, G as for launch_gather_light; out_vs: 64-bit words between the output
+// rows of consecutive vertices, 0 = B * Chs * Ld)
 // Chain version: after the fused step the same warp runs the chain's following
 // p = 1 steps (leaf children) for the vertex, out_j[S] = sum over c in S of
 // out_{j-1}[S \ {c}] * hist[c].  The rows of vertex v for step j start at
@@ -120,6 +129,12 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Ld, int64_t v0, int
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
                                 const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb = 4);
+
+// The chain's p = 1 steps for the light vertices of [v0, v1) whose first-step
+// rows are at out0 + (v - v0) * out_vs (written by launch_gather_select).
+void launch_leaf_chain(cudaStream_t st, int Ld, int64_t v0, int64_t v1, int64_t split, const int64_t *row_ptr, int B,
+                       int k, const uint64_t *out0, int64_t out_vs, int64_t Chs, const LeafChain &chain,
+                       const uint32_t *hist, unsigned long long *next);
 
 // a = 1 combine for heavy vertices [h0, h1) of the heavy list (aggregates from the task path)
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,

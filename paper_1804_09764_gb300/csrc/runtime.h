@@ -99,7 +99,9 @@ struct PlanInstance {
     int Lmax = 1;
     int64_t V = 0;          // vertices per block
     std::vector<std::pair<int64_t, int64_t>> blocks;
-    struct BlockHeavy { int64_t h0, h1, t0, t1; };
+    // heavy vertices [h0, h1) of the heavy list, their tasks [t0, t1), and the
+    // edges of their neighbour lists
+    struct BlockHeavy { int64_t h0, h1, t0, t1, edges; };
     std::vector<BlockHeavy> heavy;
     int64_t split = 1024;
     int64_t max_tasks = 0;
@@ -121,9 +123,22 @@ struct PlanInstance {
     bool tuned = false;
     struct Trial { int chain, step, mode; cudaEvent_t a, b; };
     std::vector<Trial> trials;
+    // Root chains and templates.  Every distinct root chain sums into its own
+    // totals slot (n_slots x B x L_root values per pass).  Template r of the
+    // plan (one, or several sharing their colourings) reads slot tmpl_slot[r],
+    // keeps its low tmpl_L[r] limbs (exact: its total is below 2^(64 tmpl_L[r]))
+    // and divides by tmpl_aut[r].
+    int n_slots = 1;
+    std::vector<int> chain_slot;     // per chain: totals slot, -1 for non-root chains
+    std::vector<int> tmpl_slot, tmpl_L, tmpl_root;
+    std::vector<int64_t> tmpl_aut;
+    // several templates: chains and gathered updates per colouring had each
+    // been planned alone
+    int sep_chains = 0;
+    double sep_updates = 0;
 };
 
-enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_SELECT, K_CHIST, K_KINDS };
+enum KernelKind { K_COLOUR = 0, K_HIST, K_GATHER, K_COMBINE, K_REDUCE, K_FUSED, K_SELECT, K_CHIST, K_HEAVY, K_KINDS };
 
 struct KernelTimer {
     bool on = false;
@@ -192,6 +207,13 @@ struct CountJob {
 // plan (with workspace sizing) for a count with n_iter colourings
 cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
                     std::unique_ptr<PlanInstance> *out);
+// one plan for several templates with the same k over the same colourings:
+// rooted subtrees with equal canonical forms share one table
+cc_status make_plan_multi(Ctx *c, int64_t gid, const std::vector<int64_t> &tids, int n_iter, int width_bits,
+                          cudaStream_t st, std::unique_ptr<PlanInstance> *out);
+// counts of several templates (counts, maps: [template][colouring][cap]; res: [template])
+cc_status count_multi_sync(Ctx *c, int64_t gid, const std::vector<int64_t> &tids, const CountJob &job,
+                           uint64_t *counts, int32_t cap, uint64_t *maps, cc_result *res);
 void free_plan(Ctx *c, PlanInstance *p);
 
 // Runs passes [pass0, pass1) of a job on stream st using workspace ws.
@@ -202,10 +224,11 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
                      const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out,
                      CachedPlan *graph = nullptr);
 
-// Host post-processing: copies, estimate, median of means, writes caller buffers.
+// Host post-processing for template tr of the plan: copies, estimate, median
+// of means, writes caller buffers.
 cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
                         const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
-                        uint64_t *sample_out, cc_result *res);
+                        uint64_t *sample_out, cc_result *res, int tr = 0);
 
 cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
                      uint64_t *maps, uint64_t *sample_out, cc_result *res);

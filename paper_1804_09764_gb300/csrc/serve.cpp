@@ -170,7 +170,7 @@ bool admit(Ctx *c, Server *s, Request *r)
     r->plan->tuned = true;  // served passes use the tuned variants if a count tuned them, else the defaults
     r->npass = (r->job.n_iter + r->plan->B - 1) / r->plan->B;
     if (cudaMallocHost(&r->hp, sizeof(ColourParams) * r->npass) != cudaSuccess ||
-        cudaMallocHost(&r->ht, (size_t)8 * r->npass * r->plan->B * r->plan->L_root) != cudaSuccess ||
+        cudaMallocHost(&r->ht, (size_t)8 * r->npass * r->plan->B * r->plan->L_root * r->plan->n_slots) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         complete(c, s, r, CC_ERR_CUDA, "pinned buffer or event creation failed");

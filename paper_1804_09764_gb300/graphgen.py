@@ -207,7 +207,55 @@ def prufer_tree(k: int, seed: int) -> list[tuple[int, int]]:
     if k == 2:
         return [(0, 1)]
     rng = np.random.default_rng(seed)
-    seq = [int(x) for x in rng.integers(0, k, size=k - 2)]
+    return _prufer_decode(k, [int(x) for x in rng.integers(0, k, size=k - 2)])
+
+
+def _tree_form(k: int, edges) -> str:
+    """Canonical string of an unlabelled tree: nested sorted child forms from
+    its centre (the smaller of the two forms for a bicentral tree)."""
+    adj = [[] for _ in range(k)]
+    for a, b in edges:
+        adj[a].append(b)
+        adj[b].append(a)
+    deg = [len(x) for x in adj]
+    layer = [v for v in range(k) if deg[v] <= 1]
+    left = k
+    while left > 2:
+        left -= len(layer)
+        nxt = []
+        for v in layer:
+            for u in adj[v]:
+                deg[u] -= 1
+                if deg[u] == 1:
+                    nxt.append(u)
+        layer = nxt
+
+    def form(v, parent):
+        return "(" + "".join(sorted(form(u, v) for u in adj[v] if u != parent)) + ")"
+
+    return min(form(c, -1) for c in layer)
+
+
+def all_trees(k: int) -> list[list[tuple[int, int]]]:
+    """One labelled representative of every tree on k vertices (k <= 8), in
+    the order of their first Pruefer sequence (lexicographic)."""
+    import itertools
+
+    if not 1 <= k <= 8:
+        raise ValueError("all_trees enumerates Pruefer sequences: k must be in 1..8")
+    if k <= 2:
+        return [[] if k == 1 else [(0, 1)]]
+    seen, out = set(), []
+    for seq in itertools.product(range(k), repeat=k - 2):
+        e = _prufer_decode(k, list(seq))
+        f = _tree_form(k, e)
+        if f not in seen:
+            seen.add(f)
+            out.append(e)
+    return out
+
+
+def _prufer_decode(k: int, seq) -> list[tuple[int, int]]:
     degree = [1] * k
     for x in seq:
         degree[x] += 1

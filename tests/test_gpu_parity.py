@@ -328,6 +328,47 @@ def test_leaf_chain_after_fused_step(fused):
     c.close()
 
 
+@pytest.mark.parametrize("chunks", [1, 2, 3, 7, 64])
+@pytest.mark.parametrize("fused", [0, 1])
+def test_column_segments(chunks, fused):
+    # rows split into `chunks` column segments, run segment-major (64: more
+    # segments than warp sweeps, so trailing segments are empty); chains of leaf
+    # steps after a fused step take the separate leaf kernel when chunks > 1
+    g = gg.rmat_graph(11, seed=46)
+    k = 10
+    broom = [(0, 1), (1, 2), (2, 3)] + [(0, j) for j in range(4, 10)]
+    cat = gg.template_edges("caterpillar10")[1]
+    c = make_ctx(col_chunks=chunks, fused=fused, split_threshold=10, batch=2, block_vertices=600)
+    gid = c.graph_load(g)
+    for e, root in [(broom, 0), (cat, 2)]:
+        tid = c.template_load(k, e, root)
+        res = c.count(gid, tid, seed=23, n_iter=2, want_maps=True)
+        assert res["maps"] == [O.count_maps(g, k, e, root, seed=23, j=j) for j in range(2)]
+    c.close()
+
+
+@pytest.mark.parametrize("split", [8, 1 << 20])
+def test_kernel_stats_time_heavy_vertices_apart(split):
+    # the Algorithm 4 path (vertices with more than `split` neighbours) is its own
+    # kind; with no such vertex it launches nothing
+    g = gg.rmat_graph(10, seed=62)
+    k, e = gg.template_edges("tree12")
+    c = make_ctx(split_threshold=split, timing=1)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 1)
+    c.count(gid, tid, seed=3, n_iter=2)
+    st = c.kernel_stats()
+    kinds = [n for n in st if n != "total_launches"]
+    assert kinds == ["colour", "hist", "gather", "combine", "reduce", "fused", "select", "combine_hist", "heavy"]
+    assert st["fused"]["launches"] > 0 and st["fused"]["bytes"] > 0
+    if split == 8:
+        assert st["heavy"]["launches"] > 0 and st["heavy"]["bytes"] > 0
+    else:
+        assert st["heavy"]["launches"] == 0
+    assert sum(st[n]["launches"] for n in kinds) <= st["total_launches"]
+    c.close()
+
+
 @pytest.mark.parametrize("order", [0, 1])
 def test_vertex_orders_give_identical_counts_and_samples(order):
     g = gg.rmat_graph(10, seed=61)

@@ -2,6 +2,7 @@
 symbol of include/cc.h, the planner's cost model reproduces Table 4, the
 library's automorphism count (AHU canonical forms) agrees with the oracle's
 backtracking count, and the input generators behave."""
+import math
 import os
 import re
 
@@ -103,3 +104,60 @@ def test_prufer_trees_are_trees():
         e = gg.prufer_tree(k, k)
         assert len(e) == k - 1
         assert O.automorphisms(k, e) >= 1  # raises if not a tree
+
+
+# ------------------------------------------------ Algorithm 1's sample size
+
+def _group_failure(s, k, eps):
+    """Exact probability that the mean of s colourings misses (1 +- eps) N when
+    G is T itself: one copy, colourful with probability p = k!/k^k, so the
+    colourful count is Bernoulli(p) and the group mean is Binomial(s, p) / (s p)."""
+    binom = pytest.importorskip("scipy.stats").binom
+    p = math.factorial(k) / k ** k
+    c = np.arange(s + 1)
+    return float(binom.pmf(c, s, p)[np.abs(c / (s * p) - 1) > eps].sum())
+
+
+@pytest.mark.parametrize("k,eps,delta", [(2, 0.5, 0.1), (3, 0.5, 0.05), (4, 1.0, 0.2), (5, 0.8, 0.1),
+                                         (3, 0.25, 0.01), (6, 1.5, 0.3)])
+def test_iterations_for_meets_the_guarantee_where_the_variance_bound_is_tight(lib, k, eps, delta):
+    # G = T attains Var X / (E X)^2 = 1/p - 1, the bound the sample size rests on;
+    # the failure probabilities there are computed exactly from binomial tails
+    binom = pytest.importorskip("scipy.stats").binom
+    n, t = cc.cc_iterations_for(k, eps, delta)
+    s = n // t
+    assert n == s * t and s >= 1 and t >= 1
+    pg = _group_failure(s, k, eps)
+    assert pg <= 0.25
+    # the median of t group means is off only if at least half of the groups are
+    assert binom.sf(math.ceil(t / 2) - 1, t, pg) <= delta
+
+
+def test_iterations_for_pin_rejects_a_group_size_without_the_colourful_probability(lib):
+    # a plausible slip, s = 4 / eps^2 (dropping 1/p - 1), fails the exact check
+    k, eps = 5, 0.8
+    assert _group_failure(math.ceil(4 / eps ** 2), k, eps) > 0.25
+
+
+def test_iterations_for_limits_and_errors(lib):
+    assert cc.cc_iterations_for(1, 0.1, 0.5)[0] == cc.cc_iterations_for(1, 0.1, 0.5)[1]  # k = 1: no variance
+    n1, t1 = cc.cc_iterations_for(6, 0.5, 0.1)
+    n2, t2 = cc.cc_iterations_for(6, 0.25, 0.1)
+    n3, t3 = cc.cc_iterations_for(6, 0.5, 0.01)
+    assert t1 == t2 and n2 > 3 * n1 and t3 > t1 and n3 > n1
+    for k, eps, delta, status in [(0, 0.5, 0.1, -4), (17, 0.5, 0.1, -4), (4, 0.0, 0.1, -1), (4, -1.0, 0.1, -1),
+                                  (4, 0.5, 0.0, -1), (4, 0.5, 1.0, -1), (4, float("nan"), 0.1, -1),
+                                  (16, 1e-6, 1e-9, -11)]:
+        with pytest.raises(cc.CCError) as ei:
+            cc.cc_iterations_for(k, eps, delta)
+        assert ei.value.status == status
+
+
+def test_all_trees_counts_match_the_number_of_free_trees():
+    # unlabelled trees on k vertices: 1, 1, 1, 2, 3, 6, 11 for k = 1..7 (Otter)
+    for k, want in zip(range(1, 8), [1, 1, 1, 2, 3, 6, 11]):
+        trees = gg.all_trees(k)
+        assert len(trees) == want
+        for e in trees:
+            assert len(e) == k - 1
+            assert O.automorphisms(k, e) >= 1  # a tree on 0..k-1 (the oracle checks connectivity)
