@@ -393,7 +393,8 @@ def main():
     ap.add_argument("--multi", action="store_true",
                     help="graphlet-frequency run: all 11 trees on 7 vertices, merged vs one count each")
     ap.add_argument("--col-chunks", type=int, default=0,
-                    help="column segments per neighbour row in the persistent gathers (0: ~1.5 KiB each, 1: whole rows)")
+                    help="column segments per neighbour row in the persistent gathers (0: one warp sweep each, "
+                         "whole rows in the fused kernels; 1: whole rows)")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=50.0)

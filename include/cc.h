@@ -90,8 +90,10 @@ typedef struct cc_options {
                                   (hub rows contiguous); 1: input order */
     int32_t col_chunks;        /* column segments per neighbour row in the persistent gathers
                                   (segment-major work order, so hub rows' segments are reused
-                                  from L2): 0 (default) about 1.5 KiB per segment (at most
-                                  16), 1 whole rows */
+                                  from L2).  0 (default): one 128-value warp sweep per segment
+                                  (at most 16) for the heavy-vertex task gathers and the
+                                  unfused gathers, whole rows for the fused gather + select
+                                  kernels; n > 0: n segments everywhere (1: whole rows) */
     int32_t reserved[3];
 } cc_options;
 

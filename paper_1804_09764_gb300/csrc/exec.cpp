@@ -87,6 +87,19 @@ cc_status hom_bounds(Ctx *c, Graph *g, const TemplatePlan &tp, cudaStream_t st, 
 // claims on the work counter when every row is split into segments)
 static int vertex_group(int nch) { return nch > 1 ? 4 : 1; }
 
+// Split of the light vertices of a block [v0, v1) for the fused kernels:
+// [v0, vmid) with *nch column segments, [vmid, v1) whole rows.  Whole rows
+// unless col_chunks > 0 asks for segments: their items are mostly low-degree
+// vertices, for which every segment repeats the row-pointer -> neighbour-id
+// -> row chain of dependent loads, and a chain's leaf steps then need a kernel
+// of their own (R-MAT s22 / tree-12, two steps: whole rows 8.2 s; every light
+// vertex segmented 9.5 s; only those of degree >= 64 segmented 8.55 s).
+static int64_t fused_split(const Ctx *c, int64_t v0, int64_t v1, int64_t R, int Ls, int *nch)
+{
+    *nch = c->opt.col_chunks > 0 ? column_segments(R, Ls, c->opt.col_chunks) : 1;
+    return *nch > 1 ? v1 : v0;
+}
+
 int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(l2, 1000.0))); }
 
 struct Layout {
@@ -679,22 +692,31 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     return b;
                 };
                 const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
-                const int nch = column_segments(R, Ls, c->opt.col_chunks);
+                // [v0, vmid): column-segmented gather + select into the slots, then the
+                // leaf kernel; [vmid, v1): the one-kernel chain (whole rows)
+                int nch = 1;
+                const int64_t vmid = fused_split(c, v0, v1, R, Ls, &nch);
+                int nl = 0;
                 Ln.begin(K_FUSED);
-                if (nch == 1) {
-                    // one kernel; it indexes colours and histograms by global vertex id
-                    launch_gather_select_chain(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
-                                               Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, vstride(0, Chs0), lc,
-                                               hist, next_counter());
-                } else {
-                    // column-segmented gather + select into the slots, then the leaf steps
-                    launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
+                if (vmid > v0) {
+                    launch_gather_select(st, Ls, L, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
                                          Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, next_counter(), 4, nch,
                                          vertex_group(nch), vstride(0, Chs0));
-                    launch_leaf_chain(st, L, v0, v1, p->split, g->row_ptr, B, k, out0, vstride(0, Chs0), Chs0, lc, hist,
-                                      next_counter());
+                    launch_leaf_chain(st, L, v0, vmid, p->split, g->row_ptr, B, k, out0, vstride(0, Chs0), Chs0, lc,
+                                      hist, next_counter());
+                    nl += 2;
                 }
-                Ln.end(nch == 1 ? 1 : 2, chain_bytes(e_blk - (double)hv.edges, (double)(nv - nh)));
+                if (v1 > vmid) {
+                    // rows of vertex v stay at (v - v0) * stride: shift the outputs by vmid - v0
+                    LeafChain lt = lc;
+                    for (int j = 0; j < lt.n; j++) lt.out[j] += (vmid - v0) * lt.vs[j];
+                    launch_gather_select_chain(st, Ls, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
+                                               Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col,
+                                               out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt, hist,
+                                               next_counter());
+                    nl++;
+                }
+                Ln.end(nl, chain_bytes(e_blk - (double)hv.edges, (double)(nv - nh)));
                 if (nh > 0) {
                     // heavy vertices (Algorithm 4): tasks, partial-row sums, select, leaf steps
                     Ln.begin(K_HEAVY);
@@ -748,11 +770,18 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const double light_bytes = sel_bytes(e_blk - (double)hv.edges, (double)(nv - (hv.h1 - hv.h0)));
                     Ln.begin(K_FUSED);
                     const auto site = std::make_pair((int)ci, (int)si);
-                    const int nch = column_segments(R, Ls, c->opt.col_chunks);
+                    int nch = 1;
+                    const int64_t vmid = fused_split(c, v0, v1, R, Ls, &nch);
+                    // [v0, vmid) column-segmented, [vmid, v1) whole rows
                     auto fused_run = [&](int nb) {
-                        launch_gather_select(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch,
-                                             Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(), nb, nch,
-                                             vertex_group(nch));
+                        if (vmid > v0)
+                            launch_gather_select(st, Ls, L, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
+                                                 Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(),
+                                                 nb, nch, vertex_group(nch));
+                        if (v1 > vmid)
+                            launch_gather_select(st, Ls, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
+                                                 Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col,
+                                                 out + (vmid - v0) * B * Chs * L, next_counter(), nb);
                     };
                     int nl = 0, nb_tasks = 2;
                     if (tune) {

@@ -1438,9 +1438,10 @@ void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1
 
 int column_segments(int64_t R, int Ls, int requested)
 {
+    (void)Ls;
     if (requested > 0) return std::min(requested, 64);
-    const int64_t bytes = R * 8 * Ls;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(16, bytes / 1536));
+    // one warp sweep (32 lanes x 4 values) per segment, at most 16 segments
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, (R + 127) / 128));
 }
 
 void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64_t v0, int64_t t0,

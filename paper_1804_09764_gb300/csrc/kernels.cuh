@@ -48,7 +48,8 @@ void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1
                          int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr,
                          int nb = 4, int nch = 1);
 
-// column segments for rows of R values of Ls limbs: 0 = about 3 KiB per segment
+// column segments for rows of R values of Ls limbs: requested > 0 as given
+// (<= 64); 0: one 128-value warp sweep per segment, at most 16
 int column_segments(int64_t R, int Ls, int requested);
 
 // Vectorised warp versions (16-byte loads, several neighbours in flight) for

@@ -347,6 +347,23 @@ def test_column_segments(chunks, fused):
     c.close()
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_default_segments_with_hubs(fused):
+    # default col_chunks: segmented task and unfused gathers, whole-row fused
+    # kernels; rows of 8 colourings are large enough for several segments
+    g = gg.rmat_graph(12, seed=47)
+    k = 10
+    broom = [(0, 1), (1, 2), (2, 3)] + [(0, j) for j in range(4, 10)]
+    deg = np.diff(g.row_ptr)
+    assert ((deg >= 64) & (deg <= 1024)).sum() > 20
+    c = make_ctx(fused=fused, batch=8, block_vertices=1500)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, broom, 0)
+    res = c.count(gid, tid, seed=29, n_iter=8, want_maps=True)
+    assert res["maps"] == [O.count_maps(g, k, broom, 0, seed=29, j=j) for j in range(8)]
+    c.close()
+
+
 @pytest.mark.parametrize("split", [8, 1 << 20])
 def test_kernel_stats_time_heavy_vertices_apart(split):
     # the Algorithm 4 path (vertices with more than `split` neighbours) is its own
