@@ -37,49 +37,123 @@ int bits_for(double v)
 // sum_{u in N(v)} H_c(u), H_leaf = 1.  Every table entry X_x[v][S] counts a
 // subset of these maps, so max_v H_x bounds the table and sum_v H_root bounds
 // the total.
+int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(l2, 1000.0))); }
+
+// cache key of a chain's bounds: its rooted form and its steps' children
+static std::string hom_key(const TemplatePlan &tp, int i)
+{
+    std::string key = tp.chains[i].canon + "|";
+    for (auto &s : tp.chains[i].steps) key += (s.src_chain < 0 ? std::string("()") : tp.chains[s.src_chain].canon) + ";";
+    return key;
+}
+
 cc_status hom_bounds(Ctx *c, Graph *g, const TemplatePlan &tp, cudaStream_t st, std::vector<double> *log2max,
-                     double *log2sum_root)
+                     double *log2sum_root, std::vector<std::vector<std::pair<double, double>>> *step_log2)
 {
     const int nc = (int)tp.chains.size();
     log2max->assign(nc, 0.0);
     bool all = true;
-    for (int i = 0; i < nc; i++) {
-        auto it = g->hom_cache.find(tp.chains[i].canon);
-        if (it == g->hom_cache.end()) all = false;
-    }
+    for (int i = 0; i < nc; i++)
+        if (g->hom_cache.find(hom_key(tp, i)) == g->hom_cache.end()) all = false;
     if (!all) {
+        int nsteps = 0;
+        for (auto &C : tp.chains) nsteps += (int)C.steps.size();
         std::vector<double *> H(nc, nullptr);
-        double *red = (double *)arena_alloc(c, 16);
-        bool ok = red != nullptr;
+        double *F = (double *)arena_alloc(c, sizeof(double) * std::max<int64_t>(g->n_act, 1));
+        double *red = (double *)arena_alloc(c, 32 * (size_t)(nsteps + nc));
+        bool ok = F && red;
         for (int i = 0; i < nc && ok; i++) {
             H[i] = (double *)arena_alloc(c, sizeof(double) * std::max<int64_t>(g->n_act, 1));
             ok = H[i] != nullptr;
         }
         if (!ok) {
             for (auto p : H) c->arena.free(p);
+            c->arena.free(F);
             c->arena.free(red);
             return fail(CC_ERR_BUDGET, "no room for the homomorphism bound vectors");
         }
+        // per step: (max, sum) of the bound after it and of its factor
+        CC_CUDA(cudaMemsetAsync(red, 0, 32 * (size_t)(nsteps + nc), st));
+        int q = 0;
         for (int i = 0; i < nc; i++) {
             launch_fill_double(st, g->n_act, 1.0, H[i]);
-            for (auto &s : tp.chains[i].steps)
+            for (auto &s : tp.chains[i].steps) {
                 launch_hom_step(st, g->n_act, g->row_ptr, g->col_idx, s.src_chain < 0 ? nullptr : H[s.src_chain],
-                                H[i]);
-            double ms[2] = {0, 0};
-            CC_CUDA(cudaMemsetAsync(red, 0, 16, st));
-            launch_max_sum(st, g->n_act, H[i], red);
-            CC_CUDA(cudaMemcpyAsync(ms, red, 16, cudaMemcpyDeviceToHost, st));
-            CC_CUDA(cudaStreamSynchronize(st));
-            c->launches += 3 + (int64_t)tp.chains[i].steps.size();
-            g->hom_cache[tp.chains[i].canon] = {ms[0] > 0 ? std::log2(ms[0]) : -1.0,
-                                                ms[1] > 0 ? std::log2(ms[1]) : -1.0};
+                                H[i], F);
+                launch_max_sum(st, g->n_act, H[i], red + 4 * q);
+                launch_max_sum(st, g->n_act, F, red + 4 * q + 2);
+                q++;
+            }
+            c->launches += 1 + 3 * (int64_t)tp.chains[i].steps.size();
+        }
+        std::vector<double> h(4 * (size_t)q);
+        CC_CUDA(cudaMemcpyAsync(h.data(), red, 32 * (size_t)q, cudaMemcpyDeviceToHost, st));
+        CC_CUDA(cudaStreamSynchronize(st));
+        auto l2 = [](double x) { return x > 0 ? std::log2(x) : -1.0; };
+        q = 0;
+        for (int i = 0; i < nc; i++) {
+            Graph::HomBound hb;
+            for (size_t si = 0; si < tp.chains[i].steps.size(); si++, q++) {
+                hb.steps.push_back({l2(h[4 * q]), l2(h[4 * q + 2])});
+                hb.l2max = l2(h[4 * q]);
+                hb.l2sum = l2(h[4 * q + 1]);
+            }
+            g->hom_cache[hom_key(tp, i)] = hb;
         }
         CC_CUDA(cudaGetLastError());
         for (auto p : H) c->arena.free(p);
+        c->arena.free(F);
         c->arena.free(red);
     }
-    for (int i = 0; i < nc; i++) (*log2max)[i] = g->hom_cache[tp.chains[i].canon].first;
-    *log2sum_root = g->hom_cache[tp.chains[nc - 1].canon].second;
+    if (step_log2) step_log2->assign(nc, {});
+    for (int i = 0; i < nc; i++) {
+        const auto &hb = g->hom_cache[hom_key(tp, i)];
+        (*log2max)[i] = hb.l2max;
+        if (step_log2) (*step_log2)[i] = hb.steps;
+    }
+    *log2sum_root = g->hom_cache[hom_key(tp, nc - 1)].l2sum;
+    return CC_OK;
+}
+
+// Limbs of every step's output and aggregate.  A step's values (colourful
+// maps of the partial subtree) are bounded by its homomorphism bound, its
+// aggregate by the step's factor sum_{u in N(v)} H_child(u); a step computes
+// exactly at the smallest width above its bound, or modulo 2^(64 chain_L) when
+// the bound exceeds the chain's width (which the ring maps to narrower widths
+// preserve).  Widths never decrease along a chain; the last step writes the
+// table at chain_L; an a = 1 step's output is its aggregate; a reused
+// aggregate keeps the width it was computed at.
+static cc_status step_widths(Ctx *c, Graph *g, PlanInstance *p, int width_bits, cudaStream_t st)
+{
+    const TemplatePlan &tp = p->tp;
+    const int nc = (int)tp.chains.size();
+    p->step_L.assign(nc, {});
+    p->agg_L.assign(nc, {});
+    std::vector<std::vector<std::pair<double, double>>> sl;
+    if (width_bits == 0 && tp.k >= 2 && g->n_act > 0) {
+        std::vector<double> l2max;
+        double l2sum;
+        CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum, &sl));
+    }
+    auto limbs = [](double l2) { return (bits_from_log2(l2) + 63) / 64; };
+    for (int i = 0; i < nc; i++) {
+        const auto &C = tp.chains[i];
+        const int Lc = p->chain_L[i], n = (int)C.steps.size();
+        auto &SL = p->step_L[i];
+        auto &AL = p->agg_L[i];
+        SL.assign(n, Lc);
+        AL.assign(n, Lc);
+        if (sl.empty() || (int)sl[i].size() != n) continue;  // fixed width: every step at the chain's
+        for (int si = 0; si < n; si++) {
+            int L = si + 1 == n ? Lc : std::min(Lc, limbs(sl[i][si].first));
+            if (si > 0) L = std::max(L, SL[si - 1]);
+            int A = std::min(L, std::min(Lc, limbs(sl[i][si].second)));
+            if (C.steps[si].a == 1) A = L;
+            if (C.steps[si].reuse_agg && si > 0) A = AL[si - 1];
+            SL[si] = L;
+            AL[si] = std::min(A, L);
+        }
+    }
     return CC_OK;
 }
 
@@ -100,7 +174,6 @@ static int64_t fused_split(const Ctx *c, int64_t v0, int64_t v1, int64_t R, int 
     return *nch > 1 ? v1 : v0;
 }
 
-int bits_from_log2(double l2) { return l2 < 0 ? 1 : bits_for(std::exp2(std::min(l2, 1000.0))); }
 
 struct Layout {
     uint64_t bytes = 0;
@@ -221,7 +294,7 @@ cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, 
         }
         std::vector<double> l2max;
         double l2sum;
-        CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum));
+        CC_TRY(hom_bounds(c, g, tp, st, &l2max, &l2sum, nullptr));
         const int rb = bits_from_log2(l2sum);
         if (rb > 256)
             return fail(CC_ERR_WIDTH, "exact counts may need " + std::to_string(rb) +
@@ -315,6 +388,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     p->tmpl_L = {p->L_root};
     p->tmpl_root = {p->tp.root};
     p->tmpl_aut = {p->tp.aut};
+    CC_TRY(step_widths(c, g, p.get(), width_bits, st));
     CC_TRY(finish_plan(c, g, p.get(), n_iter, width_bits, st));
     *out = std::move(p);
     return CC_OK;
@@ -389,6 +463,7 @@ cc_status make_plan_multi(Ctx *c, int64_t gid, const std::vector<int64_t> &tids,
     for (size_t ci = 0; ci < M.chains.size(); ci++)
         if (M.chains[ci].is_root) Ls[ci] = p->L_root;
     p->chain_L = Ls;
+    CC_TRY(step_widths(c, g, p.get(), width_bits, st));
     CC_TRY(finish_plan(c, g, p.get(), n_iter, width_bits, st));
     *out = std::move(p);
     return CC_OK;
@@ -729,8 +804,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const uint64_t *prev = out0;
                     int64_t prev_s = Chs0;
                     for (int j = 0; j < lc.n; j++) {
-                        launch_combine_hist(st, L, nh, B, k, lc.Ch[j], lc.Chs[j], prev_s, lc.h[j], lc.pairs[j], prev,
-                                            hrow, lc.out[j]);
+                        launch_combine_hist(st, L, L, nh, B, k, lc.Ch[j], lc.Chs[j], prev_s, lc.h[j], lc.pairs[j],
+                                            prev, hrow, lc.out[j]);
                         prev = lc.out[j];
                         prev_s = lc.Chs[j];
                     }
@@ -742,17 +817,19 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 const int64_t Ch = binom(k, s.h);
                 int64_t Chs;
                 uint64_t *out = step_out(si, &Chs);
+                // limbs of this step's output, of the previous step's rows and of the aggregate
+                const int Lo = p->step_L[ci][si], La = si > 0 ? p->step_L[ci][si - 1] : Lo, Lg = p->agg_L[ci][si];
                 if (s.src_chain < 0) {
                     const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
-                        launch_combine_select(st, L, true, v0, nv, B, k, Ch, Chs, k, p->d_rm[s.h], col, hrow, out);
-                        Ln.end(1, (double)nv * B * (Ch * 8.0 * L + 4.0 * k + 1));
+                        launch_combine_select(st, Lo, true, v0, nv, B, k, Ch, Chs, k, p->d_rm[s.h], col, hrow, out);
+                        Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + 4.0 * k + 1));
                     } else {
                         Ln.begin(K_CHIST);
-                        launch_combine_hist(st, L, nv, B, k, Ch, Chs, cur_stride, s.h, p->d_pairs.at({s.h, s.a}), cur,
-                                            hrow, out);
-                        Ln.end(1, (double)nv * B * ((Ch + binom(k, s.a)) * 8.0 * L + 4.0 * k));
+                        launch_combine_hist(st, Lo, La, nv, B, k, Ch, Chs, cur_stride, s.h, p->d_pairs.at({s.h, s.a}),
+                                            cur, hrow, out);
+                        Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + binom(k, s.a) * 8.0 * La + 4.0 * k));
                     }
                 } else if (c->opt.fused && s.a == 1 && !s.reuse_agg &&
                            !(si + 1 < C.steps.size() && C.steps[si + 1].reuse_agg)) {
@@ -764,7 +841,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
                     // algorithmic bytes: neighbour rows + ids + row pointers + output rows
                     auto sel_bytes = [&](double edges, double nvert) {
-                        return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Ch * 8.0 * L;
+                        return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Ch * 8.0 * Lo;
                     };
                     const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
                     const double light_bytes = sel_bytes(e_blk - (double)hv.edges, (double)(nv - (hv.h1 - hv.h0)));
@@ -775,13 +852,13 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     // [v0, vmid) column-segmented, [vmid, v1) whole rows
                     auto fused_run = [&](int nb) {
                         if (vmid > v0)
-                            launch_gather_select(st, Ls, L, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
+                            launch_gather_select(st, Ls, Lo, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
                                                  Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(),
                                                  nb, nch, vertex_group(nch));
                         if (v1 > vmid)
-                            launch_gather_select(st, Ls, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
+                            launch_gather_select(st, Ls, Lo, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
                                                  Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col,
-                                                 out + (vmid - v0) * B * Chs * L, next_counter(), nb);
+                                                 out + (vmid - v0) * B * Chs * Lo, next_counter(), nb);
                     };
                     int nl = 0, nb_tasks = 2;
                     if (tune) {
@@ -806,10 +883,10 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         // heavy vertices (Algorithm 4): tasks, partial-row sums, select
                         Ln.begin(K_HEAVY);
                         uint64_t *part = (uint64_t *)W(p->off_partial);
-                        launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
+                        launch_gather_tasks(st, Ls, Lo, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
                                             next_counter(), nb_tasks, column_segments(R, Ls, c->opt.col_chunks));
-                        launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
-                        launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
+                        launch_gather_reduce(st, Lo, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
+                        launch_select_heavy(st, Lo, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
                                             agg, out);
                         Ln.end(3, sel_bytes((double)hv.edges, (double)(hv.h1 - hv.h0)));
                     }
@@ -822,7 +899,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     if (!s.reuse_agg) {
                         // algorithmic bytes of this gather: neighbour rows + CSR + aggregate write
                         auto g_bytes = [&](double edges, double nvert) {
-                            return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Cp * 8.0 * L;
+                            return edges * ((double)B * Cp * 8.0 * Ls + 4) + nvert * 8.0 + nvert * B * Cp * 8.0 * Lg;
                         };
                         const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
                         const int64_t nh = hv.h1 - hv.h0;
@@ -836,15 +913,15 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                             const bool vec = !bulk && !group && (gm == 0 || gm == 2) && vec_gather_ok(Ls, R);
                             Ln.begin(K_GATHER);
                             if (bulk)
-                                launch_gather_light_bulk(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, g->nnz,
+                                launch_gather_light_bulk(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, g->nnz,
                                                          X, R, agg, err);
                             else if (group)
-                                launch_gather_light_group(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R,
+                                launch_gather_light_group(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, X, R,
                                                           agg);
                             else if (vec)
-                                launch_gather_light_vec(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
+                                launch_gather_light_vec(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg);
                             else
-                                launch_gather_light(st, Ls, L, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
+                                launch_gather_light(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
                                                     gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
                                                     column_segments(R, Ls, c->opt.col_chunks),
                                                     vertex_group(column_segments(R, Ls, c->opt.col_chunks)));
@@ -853,18 +930,18 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 Ln.begin(K_HEAVY);
                                 uint64_t *part = (uint64_t *)W(p->off_partial);
                                 if (bulk)
-                                    launch_gather_tasks_bulk(st, Ls, L, hv.t0, hv.t1, g->col_idx, g->nnz, sp.task_e, X,
+                                    launch_gather_tasks_bulk(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, g->nnz, sp.task_e, X,
                                                              R, part, err);
                                 else if (group)
-                                    launch_gather_tasks_group(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R,
+                                    launch_gather_tasks_group(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R,
                                                               part);
                                 else if (vec)
-                                    launch_gather_tasks_vec(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
+                                    launch_gather_tasks_vec(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part);
                                 else
-                                    launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
+                                    launch_gather_tasks(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
                                                         gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
                                                         column_segments(R, Ls, c->opt.col_chunks));
-                                launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
+                                launch_gather_reduce(st, Lg, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
                                 Ln.end(2, heavy_bytes);
                             }
@@ -890,13 +967,14 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     }
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
-                        launch_combine_select(st, L, false, v0, nv, B, k, Ch, Chs, Cps, p->d_rm[s.h], col, agg, out);
-                        Ln.end(1, (double)nv * B * ((Ch + Cp) * 8.0 * L + 1));
+                        // a = 1: the output is the aggregate (Lg == Lo)
+                        launch_combine_select(st, Lo, false, v0, nv, B, k, Ch, Chs, Cps, p->d_rm[s.h], col, agg, out);
+                        Ln.end(1, (double)nv * B * ((Ch + Cp) * 8.0 * Lo + 1));
                     } else {
                         Ln.begin(K_COMBINE);
-                        launch_combine_generic(st, L, nv, B, Ch, Chs, cur_stride, Cps, binom(s.h, s.a),
+                        launch_combine_generic(st, Lo, La, Lg, nv, B, Ch, Chs, cur_stride, Cps, binom(s.h, s.a),
                                                p->d_pairs.at({s.h, s.a}), cur, agg, out);
-                        Ln.end(1, (double)nv * B * (Ch + binom(k, s.a) + Cp) * 8.0 * L);
+                        Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + binom(k, s.a) * 8.0 * La + Cp * 8.0 * Lg));
                     }
                 }
                 cur = out;

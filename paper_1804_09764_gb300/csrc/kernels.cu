@@ -917,8 +917,11 @@ gather_reduce_kernel(int64_t h0, int64_t h1, int64_t v0, int64_t t0, const int32
 }
 
 // Rows carry Cs >= C columns (C rounded up to even so a row is a whole number of
-// 16-byte units); columns C..Cs-1 are written as zero.
-template <int L>
+// 16-byte units); columns C..Cs-1 are written as zero.  act rows hold La-limb
+// values, agg rows Lb-limb values, out rows L-limb values (La, Lb <= L): each
+// operand is read at the width its bound needs and the product is formed only
+// from the limb products below limb L.
+template <int L, int La, int Lb>
 __global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps,
                                        int64_t npairs, const uint32_t *__restrict__ pairs,
                                        const uint64_t *__restrict__ act, const uint64_t *__restrict__ agg,
@@ -930,27 +933,28 @@ __global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, i
         Wide<L> acc;
         wzero(acc);
         if (s < Ch) {
-            const uint64_t *ar = act + vb * Cas * L;
-            const uint64_t *pr = agg + vb * Cps * L;
+            const uint64_t *ar = act + vb * Cas * La;
+            const uint64_t *pr = agg + vb * Cps * Lb;
             // in groups of G: split entries, then both operands, then the multiply-adds
             constexpr int G = L <= 1 ? 4 : 2;
             for (int64_t q0 = 0; q0 < npairs; q0 += G) {
                 uint32_t pq[G];
 #pragma unroll
                 for (int j = 0; j < G; j++) pq[j] = q0 + j < npairs ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
-                Wide<L> x[G], y[G];
+                Wide<La> x[G];
+                Wide<Lb> y[G];
 #pragma unroll
                 for (int j = 0; j < G; j++) {
                     if (q0 + j < npairs) {
-                        x[j] = wload<L, L>(ar + (pq[j] & 0xFFFFu) * L);
-                        y[j] = wload<L, L>(pr + (pq[j] >> 16) * L);
+                        x[j] = wload<La, La>(ar + (pq[j] & 0xFFFFu) * La);
+                        y[j] = wload<Lb, Lb>(pr + (pq[j] >> 16) * Lb);
                     } else {
                         wzero(x[j]);
                         wzero(y[j]);
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < G; j++) wmac(acc, x[j], y[j]);
+                for (int j = 0; j < G; j++) wmac_mixed<L, La, Lb>(acc, x[j], y[j]);
             }
         }
         wstore(out + i * L, acc);
@@ -1012,7 +1016,8 @@ __global__ void select_heavy_kernel(int64_t h0, int64_t h1, int64_t v0, const in
     }
 }
 
-template <int L>
+// act rows hold La-limb values (La <= L)
+template <int L, int La>
 __global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Chs, int64_t Cas, int h,
                                     const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
                                     const uint32_t *__restrict__ hist, uint64_t *__restrict__ out)
@@ -1023,13 +1028,13 @@ __global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Ch
         Wide<L> acc;
         wzero(acc);
         if (s < Ch) {
-            const uint64_t *ar = act + vb * Cas * L;
+            const uint64_t *ar = act + vb * Cas * La;
             const uint32_t *hr = hist + vb * k;
 #pragma unroll 4
             for (int q = 0; q < h; q++) {
                 const uint32_t pq = __ldg(pairs + q * Ch + s);
                 const uint32_t hc = hr[pq >> 16];
-                if (hc) wmac_small(acc, wload<L, L>(ar + (pq & 0xFFFFu) * L), hc);
+                if (hc) wmac_small(acc, wload<La, L>(ar + (pq & 0xFFFFu) * La), hc);
             }
         }
         wstore(out + i * L, acc);
@@ -1109,7 +1114,7 @@ __global__ void sample_kernel(int64_t n_s, const int64_t *__restrict__ sample_v,
 
 __global__ void hom_step_kernel(int64_t n_act, const int64_t *__restrict__ row_ptr,
                                 const int32_t *__restrict__ col_idx, const double *__restrict__ Hc,
-                                double *__restrict__ H)
+                                double *__restrict__ H, double *__restrict__ F)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t v = blockIdx.x * (int64_t)kWarps + warp;
@@ -1118,7 +1123,10 @@ __global__ void hom_step_kernel(int64_t n_act, const int64_t *__restrict__ row_p
     for (int64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32) s += Hc ? Hc[col_idx[e]] : 1.0;
 #pragma unroll
     for (int d = 16; d; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-    if (lane == 0) H[v] *= s;
+    if (lane == 0) {
+        H[v] *= s;
+        if (F) F[v] = s;
+    }
 }
 
 __global__ void fill_double_kernel(int64_t n, double v, double *x)
@@ -1453,14 +1461,31 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
                           h0, h1, v0, t0, heavy_v, heavy_tptr, partial, R, agg));
 }
 
-void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Chs, int64_t Cas,
-                            int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
+void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, int B, int64_t Ch, int64_t Chs,
+                            int64_t Cas, int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
                             const uint64_t *agg, uint64_t *out)
 {
     const int64_t total = nv * B * Chs;
     if (total == 0) return;
-    CC_DISPATCH_L(L, combine_generic_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                         total, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out));
+    L = std::max(1, std::min(L, 4));
+    La = std::max(1, std::min(La, L));
+    Lb = std::max(1, std::min(Lb, L));
+    const unsigned g = grid_stride_ctas(total, 256);
+#define CC_CG(l, a, b)                                                                              \
+    case ((l - 1) * 16 + (a - 1) * 4 + (b - 1)):                                                    \
+        combine_generic_kernel<l, a, b><<<g, 256, 0, st>>>(total, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out); \
+        break;
+    switch ((L - 1) * 16 + (La - 1) * 4 + (Lb - 1)) {
+        CC_CG(1, 1, 1)
+        CC_CG(2, 1, 1) CC_CG(2, 1, 2) CC_CG(2, 2, 1) CC_CG(2, 2, 2)
+        CC_CG(3, 1, 1) CC_CG(3, 1, 2) CC_CG(3, 1, 3) CC_CG(3, 2, 1) CC_CG(3, 2, 2) CC_CG(3, 2, 3)
+        CC_CG(3, 3, 1) CC_CG(3, 3, 2) CC_CG(3, 3, 3)
+        CC_CG(4, 1, 1) CC_CG(4, 1, 2) CC_CG(4, 1, 3) CC_CG(4, 1, 4) CC_CG(4, 2, 1) CC_CG(4, 2, 2)
+        CC_CG(4, 2, 3) CC_CG(4, 2, 4) CC_CG(4, 3, 1) CC_CG(4, 3, 2) CC_CG(4, 3, 3) CC_CG(4, 3, 4)
+        CC_CG(4, 4, 1) CC_CG(4, 4, 2) CC_CG(4, 4, 3) CC_CG(4, 4, 4)
+    default: break;
+    }
+#undef CC_CG
 }
 
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
@@ -1478,13 +1503,25 @@ void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0,
     }
 }
 
-void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64_t Ch, int64_t Chs, int64_t Cas,
-                         int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist, uint64_t *out)
+void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int k, int64_t Ch, int64_t Chs,
+                         int64_t Cas, int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist,
+                         uint64_t *out)
 {
     const int64_t total = nv * B * Chs;
     if (total == 0) return;
-    CC_DISPATCH_L(L, combine_hist_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
-                         total, k, Ch, Chs, Cas, h, pairs, act, hist, out));
+    L = std::max(1, std::min(L, 4));
+    La = std::max(1, std::min(La, L));
+    const unsigned g = grid_stride_ctas(total, 256);
+#define CC_CH(l, a)                                                                                        \
+    case ((l - 1) * 4 + (a - 1)):                                                                          \
+        combine_hist_kernel<l, a><<<g, 256, 0, st>>>(total, k, Ch, Chs, Cas, h, pairs, act, hist, out); \
+        break;
+    switch ((L - 1) * 4 + (La - 1)) {
+        CC_CH(1, 1) CC_CH(2, 1) CC_CH(2, 2) CC_CH(3, 1) CC_CH(3, 2) CC_CH(3, 3)
+        CC_CH(4, 1) CC_CH(4, 2) CC_CH(4, 3) CC_CH(4, 4)
+    default: break;
+    }
+#undef CC_CH
 }
 
 namespace {
@@ -1597,10 +1634,10 @@ void launch_sample_extract(cudaStream_t st, int L, int64_t n_s, const int64_t *s
 }
 
 void launch_hom_step(cudaStream_t st, int64_t n_act, const int64_t *row_ptr, const int32_t *col_idx,
-                     const double *Hc, double *H)
+                     const double *Hc, double *H, double *F)
 {
     if (n_act == 0) return;
-    hom_step_kernel<<<grid_for(n_act, kWarps), kWarps * 32, 0, st>>>(n_act, row_ptr, col_idx, Hc, H);
+    hom_step_kernel<<<grid_for(n_act, kWarps), kWarps * 32, 0, st>>>(n_act, row_ptr, col_idx, Hc, H, F);
 }
 
 void launch_fill_double(cudaStream_t st, int64_t n, double v, double *x)

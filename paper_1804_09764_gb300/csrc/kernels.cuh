@@ -90,16 +90,20 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
 // combine kernels (Eq. 1 inner sum).  Rows: act C(k,a), agg C(k,p), out C(k,h)
 // valid columns, stored with strides Cas, Cps, Chs (>= the column counts; extra
 // output columns are written as zero); B rows per vertex.
-void launch_combine_generic(cudaStream_t st, int L, int64_t nv, int B, int64_t Ch, int64_t Chs, int64_t Cas,
-                            int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
+// act rows of La-limb values, agg rows of Lb-limb values, out rows of L limbs
+// (La, Lb <= L)
+void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, int B, int64_t Ch, int64_t Chs,
+                            int64_t Cas, int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
                             const uint64_t *agg, uint64_t *out);
 // a = 1: act is the single vertex v with colour col(v)
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
                            int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
                            const void *agg, uint64_t *out);
-// p = 1: agg is the colour histogram of N(v); pairs = the (h, h-1) split table
-void launch_combine_hist(cudaStream_t st, int L, int64_t nv, int B, int k, int64_t Ch, int64_t Chs, int64_t Cas,
-                         int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist, uint64_t *out);
+// p = 1: agg is the colour histogram of N(v); pairs = the (h, h-1) split table;
+// act rows of La-limb values (La <= L)
+void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int k, int64_t Ch, int64_t Chs,
+                         int64_t Cas, int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist,
+                         uint64_t *out);
 
 // Fused table gather + a = 1 combine for the light vertices of [v0, v1) (persistent
 // warps on the zeroed counter `next`): out[v][b][T u {col}] = sum_u X[u][b][T].
@@ -150,9 +154,10 @@ void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_
 void launch_sample_extract(cudaStream_t st, int L, int64_t n_s, const int64_t *sample_v,
                            int64_t v0, int64_t v1, int B, const uint64_t *root, uint64_t *out);
 
-// homomorphism bound: H[v] *= sum_{u in N(v)} Hc[u]  (Hc == nullptr: all ones)
+// homomorphism bound: H[v] *= sum_{u in N(v)} Hc[u]  (Hc == nullptr: all ones);
+// F (if not null) receives the factor sum_{u in N(v)} Hc[u]
 void launch_hom_step(cudaStream_t st, int64_t n_act, const int64_t *row_ptr, const int32_t *col_idx,
-                     const double *Hc, double *H);
+                     const double *Hc, double *H, double *F = nullptr);
 void launch_fill_double(cudaStream_t st, int64_t n, double v, double *x);
 // out[0] = max, out[1] = sum (out must be zeroed)
 void launch_max_sum(cudaStream_t st, int64_t n, const double *x, double *out);

@@ -65,8 +65,15 @@ struct Graph {
     // host copies used for planning
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_new_id;  // original id -> compact id or -1 (isolated)
-    // homomorphism bounds cache: canonical form -> (log2 max_v, log2 sum_v)
-    std::map<std::string, std::pair<double, double>> hom_cache;
+    // homomorphism bounds cache, keyed by a chain's rooted canonical form and
+    // the forms of the children it attaches in step order: log2 of max_v and
+    // sum_v of the final bound, and per step log2 max_v of the bound after the
+    // step and of the step's factor sum_{u in N(v)} H_child(u)
+    struct HomBound {
+        double l2max = -1, l2sum = -1;
+        std::vector<std::pair<double, double>> steps;
+    };
+    std::map<std::string, HomBound> hom_cache;
     // heavy-vertex task lists per split threshold
     struct Split {
         int64_t s = 0;
@@ -96,6 +103,9 @@ struct PlanInstance {
     bool exact = true;
     int L_root = 1;
     std::vector<int> chain_L;
+    // per chain and step: limbs of the step's output rows and of its aggregate
+    // (the last step's output is the chain's table, chain_L limbs)
+    std::vector<std::vector<int>> step_L, agg_L;
     int Lmax = 1;
     int64_t V = 0;          // vertices per block
     std::vector<std::pair<int64_t, int64_t>> blocks;

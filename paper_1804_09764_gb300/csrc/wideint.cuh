@@ -69,6 +69,38 @@ __device__ __forceinline__ void wmac(Wide<L> &acc, const Wide<L> &a, const Wide<
 }
 
 // acc += a * s for a small multiplier s (< 2^32 in use: colour histogram counts)
+// acc += a * b mod 2^(64 L) for an La-limb a and an Lb-limb b (La, Lb <= L):
+// schoolbook over the La x Lb limb products that land below limb L; the carry
+// out of row i goes to limb i + Lb (still zero), or is dropped at limb L.
+template <int L, int La, int Lb>
+__device__ __forceinline__ void wmac_mixed(Wide<L> &acc, const Wide<La> &a, const Wide<Lb> &b)
+{
+    static_assert(La <= L && Lb <= L, "operands wider than the result");
+    if constexpr (L == 1) {
+        acc.w[0] += a.w[0] * b.w[0];
+    } else {
+        Wide<L> p;
+        wzero(p);
+#pragma unroll
+        for (int i = 0; i < La; i++) {
+            uint64_t carry = 0;
+#pragma unroll
+            for (int j = 0; j < Lb && i + j < L; j++) {
+                const uint64_t lo = a.w[i] * b.w[j];
+                const uint64_t hi = (i + j + 1 < L) ? __umul64hi(a.w[i], b.w[j]) : 0;
+                const uint64_t t = p.w[i + j] + lo;
+                uint64_t c1 = t < lo;
+                const uint64_t sum = t + carry;
+                c1 += sum < carry;
+                p.w[i + j] = sum;
+                carry = hi + c1;
+            }
+            if (i + Lb < L) p.w[i + Lb] = carry;
+        }
+        wadd(acc, p);
+    }
+}
+
 template <int L>
 __device__ __forceinline__ void wmac_small(Wide<L> &acc, const Wide<L> &a, uint64_t s)
 {

@@ -364,6 +364,37 @@ def test_default_segments_with_hubs(fused):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def hub_of_stars():
+    # hub 0 - 300 middle vertices - 250 leaves each: aggregates ~75,300 at the hub
+    M, P = 300, 250
+    edges = [(0, 1 + i) for i in range(M)]
+    nid = 1 + M
+    for i in range(M):
+        for _ in range(P):
+            edges.append((1 + i, nid))
+            nid += 1
+    return gg.csr_from_edges(nid, np.array(edges))
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_mixed_width_steps(hub_of_stars, fused):
+    # spider with five legs of length 2, rooted at its centre: the bounds after
+    # 3, 4 and 5 legs are ~4e14, ~3e19 and ~2e24, so the root chain's steps run
+    # at 1, 1, 1, 2 and 2 limbs with one-limb aggregates (the generic combine
+    # multiplies 1x1 and 2x1 limbs into 2); the map counts exceed 2^64
+    g = hub_of_stars
+    spider = [(0, 1), (1, 2), (0, 3), (3, 4), (0, 5), (5, 6), (0, 7), (7, 8), (0, 9), (9, 10)]
+    maps = [O.count_maps(g, 11, spider, 0, seed=3, j=j) for j in range(2)]
+    assert max(maps) >= 1 << 64
+    c = make_ctx(fused=fused, batch=2)
+    gid = c.graph_load(g)
+    tid = c.template_load(11, spider, 0)
+    res = c.count(gid, tid, seed=3, n_iter=2, want_maps=True)
+    assert res["limbs"] == 2 and res["maps"] == maps
+    c.close()
+
+
 @pytest.mark.parametrize("split", [8, 1 << 20])
 def test_kernel_stats_time_heavy_vertices_apart(split):
     # the Algorithm 4 path (vertices with more than `split` neighbours) is its own
