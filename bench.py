@@ -45,6 +45,8 @@ WORKLOADS = {
     # root 1, the planner's root for the scale-22 headline)
     "rmat18_tree12": dict(graph=("rmat", 18, 18), template="tree12", root=1, n_iter=1, budget=16 << 30),
     "rmat24_spider15": dict(graph=("rmat", 24, 24), template="spider15", root=0, n_iter=4, budget=150 << 30),
+    # small case of the spider-15 combine for profiler captures (a few GB)
+    "rmat16_spider15": dict(graph=("rmat", 16, 16), template="spider15", root=0, n_iter=1, budget=6 << 30),
 }
 DEFAULT = "rmat22_tree12"
 
@@ -507,6 +509,17 @@ def main():
                 "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "launches": d["launches"], "avg_launch_ms": 1e3 * d["seconds"] / d["launches"],
                 "share_of_kernel_time": d["seconds"] / sum(v["seconds"] for v in kinds.values())}
+    if dname == "combine" and info["limb_products_per_colouring"] > 0:
+        # the general combine is bound by its wide multiply-adds: 64-bit limb
+        # products per second against the rate the GPU sustains on registers
+        lp = info["limb_products_per_colouring"] * n_iter * args.steps
+        alu_peak = ctx.limb_product_rate()
+        a_alu = lp / d["seconds"] / 1e12
+        roofline.update({"bound": "alu", "achieved": a_alu, "peak": alu_peak / 1e12,
+                         "unit": "T limb-products/s", "frac": a_alu / (alu_peak / 1e12),
+                         "peak_kind": "measured (cc_limb_product_rate: register-resident 64-bit multiply-adds)",
+                         "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
+                         "limb_products_per_launch": lp / d["launches"]})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         s, dt, desc, gs, k2, e2, root2 = oracle_sample(wl, target_s=15.0)

@@ -199,6 +199,11 @@ typedef struct cc_plan_info {
     double pairs_per_colouring;      /* combine multiply-adds per colouring */
     uint64_t workspace_bytes;
     int64_t table4_memory, table4_computation;  /* Table 4 cost numbers of the partition */
+    double limb_products_per_colouring;  /* 64-bit limb multiplications of the general combines
+                                            (a >= 2, p >= 2) at their widths: per product of an
+                                            La-limb by an Lb-limb value into L limbs, the limb
+                                            pairs i + j < L (low halves) and i + j + 1 < L (high
+                                            halves) */
 } cc_plan_info;
 
 cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out);
@@ -388,6 +393,13 @@ cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_
 
 /* |Aut(T)| from rooted canonical forms at the tree centre.  Host only. */
 cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *aut);
+
+/* The rate of 64-bit limb products (a 64 x 64-bit multiply's low and high
+ * halves counted as two, each with its carry-propagating add) that the
+ * context's GPU sustains on register operands: the arithmetic ceiling of the
+ * general combine, whose work cc_plan_info counts in the same unit.  Runs two
+ * short kernels (~10 ms) and synchronises the context's stream. */
+cc_status cc_limb_product_rate(cc_ctx *ctx, double *per_second);
 
 /* Library version string. */
 const char *cc_version(void);

@@ -21,8 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 CU_FLAGS = ARCH + ["-lineinfo", "--expt-relaxed-constexpr"] + COMMON
 
-SOURCES = ["kernels.cu", "noalloc.cu", "exec.cpp", "graph.cpp", "plan.cpp", "arena.cpp", "api.cpp", "serve.cpp",
-           "estimate.cpp"]
+SOURCES = ["kernels.cu", "combine.cu", "noalloc.cu", "exec.cpp", "graph.cpp", "plan.cpp", "arena.cpp", "api.cpp",
+           "serve.cpp", "estimate.cpp"]
 HEADERS = ["kernels.cuh", "wideint.cuh", "runtime.h", "plan.h"]
 
 

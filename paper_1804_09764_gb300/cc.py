@@ -34,7 +34,7 @@ EXPORTED = [
     "cc_count_ex", "cc_plan_info_get", "cc_kernel_stats_get", "cc_kernel_stats_reset", "cc_submit",
     "cc_poll", "cc_wait", "cc_cancel", "cc_serve_stats_get", "cc_template_cost",
     "cc_template_automorphisms", "cc_version", "cc_table_gather", "cc_table_gather_noalloc",
-    "cc_iterations_for", "cc_estimate", "cc_count_multi", "cc_multi_plan_info_get",
+    "cc_iterations_for", "cc_estimate", "cc_count_multi", "cc_multi_plan_info_get", "cc_limb_product_rate",
 ]
 
 
@@ -90,7 +90,7 @@ class cc_plan_info(ctypes.Structure):
                 ("updates_per_colouring", ctypes.c_double), ("gather_bytes_per_colouring", ctypes.c_double),
                 ("algorithmic_bytes_per_colouring", ctypes.c_double), ("pairs_per_colouring", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_uint64), ("table4_memory", ctypes.c_int64),
-                ("table4_computation", ctypes.c_int64)]
+                ("table4_computation", ctypes.c_int64), ("limb_products_per_colouring", ctypes.c_double)]
 
 
 class cc_kernel_stats(ctypes.Structure):
@@ -153,6 +153,7 @@ def load_library(path: str = LIB_PATH):
         "cc_estimate": (I32, [P, I64, I64, U64, I64, ctypes.c_double, ctypes.c_double, I64, P]),
         "cc_count_multi": (I32, [P, I64, P, I32, P, P, I32, P]),
         "cc_multi_plan_info_get": (I32, [P, I64, P, I32, I32, P]),
+        "cc_limb_product_rate": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -414,6 +415,12 @@ class Context:
         _check(self._lib.cc_estimate(self._h, gid, tid, seed & (2 ** 64 - 1), first_iter, float(epsilon),
                                      float(delta), max_iter, ctypes.byref(r)))
         return {f: getattr(r, f) for f, _ in cc_estimate_result._fields_}
+
+    def limb_product_rate(self) -> float:
+        """cc_limb_product_rate: 64-bit limb products per second on this GPU."""
+        r = ctypes.c_double()
+        _check(self._lib.cc_limb_product_rate(self._h, ctypes.byref(r)))
+        return r.value
 
     def kernel_stats_reset(self):
         _check(self._lib.cc_kernel_stats_reset(self._h))

@@ -317,6 +317,7 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->workspace_bytes = p->ws_bytes;
     out->table4_memory = p->tp.table4_memory;
     out->table4_computation = p->tp.table4_computation;
+    out->limb_products_per_colouring = p->limb_products;
     free_plan(c, p.get());
     return CC_OK;
 }
@@ -363,6 +364,21 @@ cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_
     if (rc) return fail(rc, err);
     *memory = tp.table4_memory;
     *computation = tp.table4_computation;
+    return CC_OK;
+}
+
+cc_status cc_limb_product_rate(cc_ctx *ctx, double *per_second)
+{
+    if (!ctx || !per_second) return fail(CC_ERR_INVALID_ARG, "ctx or per_second is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    uint64_t *scratch = (uint64_t *)arena_alloc(c, 256);
+    if (!scratch) return fail(CC_ERR_BUDGET, "no room for one word");
+    *per_second = limb_product_rate(c->stream, scratch);
+    c->arena.free(scratch);
+    c->launches += 2;
+    if (*per_second <= 0) return fail(CC_ERR_CUDA, "limb product rate kernel failed");
     return CC_OK;
 }
 

@@ -579,6 +579,16 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
             double pairs_v = s.a == 1 ? (double)binom(k, s.h)
                                       : (s.p == 1 ? (double)binom(k, s.h) * s.h : (double)binom(k, s.h) * binom(s.h, s.a));
             p->pairs += na * pairs_v;
+            // 64-bit limb multiplications of a general combine (a >= 2, gathered child) at its widths
+            if (s.a >= 2 && s.src_chain >= 0) {
+                const int L = p->step_L[i][&s - C.steps.data()];
+                const int La = &s == C.steps.data() ? L : p->step_L[i][&s - C.steps.data() - 1];
+                const int Lb = p->agg_L[i][&s - C.steps.data()];
+                int m = 0;
+                for (int x = 0; x < La; x++)
+                    for (int y = 0; y < Lb && x + y < L; y++) m += 1 + (x + y + 1 < L);
+                p->limb_products += na * pairs_v * m;
+            }
             if (s.src_chain >= 0 && !s.reuse_agg) {
                 double cols = (double)binom(k, s.p);
                 p->updates += nnz * cols;

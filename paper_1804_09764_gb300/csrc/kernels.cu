@@ -916,51 +916,6 @@ gather_reduce_kernel(int64_t h0, int64_t h1, int64_t v0, int64_t t0, const int32
     }
 }
 
-// Rows carry Cs >= C columns (C rounded up to even so a row is a whole number of
-// 16-byte units); columns C..Cs-1 are written as zero.  act rows hold La-limb
-// values, agg rows Lb-limb values, out rows L-limb values (La, Lb <= L): each
-// operand is read at the width its bound needs and the product is formed only
-// from the limb products below limb L.
-template <int L, int La, int Lb>
-__global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps,
-                                       int64_t npairs, const uint32_t *__restrict__ pairs,
-                                       const uint64_t *__restrict__ act, const uint64_t *__restrict__ agg,
-                                       uint64_t *__restrict__ out)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vb = i / Chs, s = i - vb * Chs;
-        Wide<L> acc;
-        wzero(acc);
-        if (s < Ch) {
-            const uint64_t *ar = act + vb * Cas * La;
-            const uint64_t *pr = agg + vb * Cps * Lb;
-            // in groups of G: split entries, then both operands, then the multiply-adds
-            constexpr int G = L <= 1 ? 4 : 2;
-            for (int64_t q0 = 0; q0 < npairs; q0 += G) {
-                uint32_t pq[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) pq[j] = q0 + j < npairs ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
-                Wide<La> x[G];
-                Wide<Lb> y[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) {
-                    if (q0 + j < npairs) {
-                        x[j] = wload<La, La>(ar + (pq[j] & 0xFFFFu) * La);
-                        y[j] = wload<Lb, Lb>(pr + (pq[j] >> 16) * Lb);
-                    } else {
-                        wzero(x[j]);
-                        wzero(y[j]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < G; j++) wmac_mixed<L, La, Lb>(acc, x[j], y[j]);
-            }
-        }
-        wstore(out + i * L, acc);
-    }
-}
-
 template <int L, bool HIST>
 __global__ void combine_select_kernel(int64_t total, int64_t v0, int B, int k, int64_t Ch, int64_t Chs, int64_t Cps,
                                       const uint16_t *__restrict__ rm, const uint8_t *__restrict__ col,
@@ -1459,33 +1414,6 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
     if (h1 <= h0) return;
     CC_DISPATCH_L(Ld, gather_reduce_kernel<LL><<<grid_for(h1 - h0, kWarps), kWarps * 32, 0, st>>>(
                           h0, h1, v0, t0, heavy_v, heavy_tptr, partial, R, agg));
-}
-
-void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, int B, int64_t Ch, int64_t Chs,
-                            int64_t Cas, int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
-                            const uint64_t *agg, uint64_t *out)
-{
-    const int64_t total = nv * B * Chs;
-    if (total == 0) return;
-    L = std::max(1, std::min(L, 4));
-    La = std::max(1, std::min(La, L));
-    Lb = std::max(1, std::min(Lb, L));
-    const unsigned g = grid_stride_ctas(total, 256);
-#define CC_CG(l, a, b)                                                                              \
-    case ((l - 1) * 16 + (a - 1) * 4 + (b - 1)):                                                    \
-        combine_generic_kernel<l, a, b><<<g, 256, 0, st>>>(total, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out); \
-        break;
-    switch ((L - 1) * 16 + (La - 1) * 4 + (Lb - 1)) {
-        CC_CG(1, 1, 1)
-        CC_CG(2, 1, 1) CC_CG(2, 1, 2) CC_CG(2, 2, 1) CC_CG(2, 2, 2)
-        CC_CG(3, 1, 1) CC_CG(3, 1, 2) CC_CG(3, 1, 3) CC_CG(3, 2, 1) CC_CG(3, 2, 2) CC_CG(3, 2, 3)
-        CC_CG(3, 3, 1) CC_CG(3, 3, 2) CC_CG(3, 3, 3)
-        CC_CG(4, 1, 1) CC_CG(4, 1, 2) CC_CG(4, 1, 3) CC_CG(4, 1, 4) CC_CG(4, 2, 1) CC_CG(4, 2, 2)
-        CC_CG(4, 2, 3) CC_CG(4, 2, 4) CC_CG(4, 3, 1) CC_CG(4, 3, 2) CC_CG(4, 3, 3) CC_CG(4, 3, 4)
-        CC_CG(4, 4, 1) CC_CG(4, 4, 2) CC_CG(4, 4, 3) CC_CG(4, 4, 4)
-    default: break;
-    }
-#undef CC_CG
 }
 
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,

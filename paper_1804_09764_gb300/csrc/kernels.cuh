@@ -99,6 +99,11 @@ void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, 
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
                            int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
                            const void *agg, uint64_t *out);
+// 64-bit limb products per second that this GPU sustains in registers (the
+// combines' multiply-add chains without their loads); synchronises st.
+// scratch: one device word.  0 on a CUDA error.
+double limb_product_rate(cudaStream_t st, uint64_t *scratch);
+
 // p = 1: agg is the colour histogram of N(v); pairs = the (h, h-1) split table;
 // act rows of La-limb values (La <= L)
 void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int k, int64_t Ch, int64_t Chs,

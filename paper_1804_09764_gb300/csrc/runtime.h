@@ -126,7 +126,7 @@ struct PlanInstance {
              off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0, off_ctr = 0;
     std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
     // analytic figures
-    double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0;
+    double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0, limb_products = 0;
     // autotuner: gather kernel variant per gather site (chain, step), chosen by
     // timing every applicable variant on the first pass
     std::map<std::pair<int, int>, int> site_mode;

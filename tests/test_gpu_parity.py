@@ -430,3 +430,11 @@ def test_vertex_orders_give_identical_counts_and_samples(order):
     assert res["maps"][0] == sum(pv)
     assert res["samples"][0] == [pv[v] for v in sample]
     c.close()
+
+
+def test_limb_product_rate():
+    # register-resident 64-bit multiply-adds: far above 1e11/s on any GB300
+    c = make_ctx()
+    r = c.limb_product_rate()
+    assert 1e11 < r < 1e15
+    c.close()
