@@ -206,6 +206,8 @@ typedef struct cc_plan_info {
                                             halves) */
 } cc_plan_info;
 
+/* Describes the plan the last cc_count of (g, t) used while it is still
+ * cached, else plans a count of opt.batch (default 16) colourings. */
 cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out);
 
 /* Per-kernel CUDA-event statistics (opt.timing = 1); cumulative since reset.

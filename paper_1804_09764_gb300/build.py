@@ -21,9 +21,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 CU_FLAGS = ARCH + ["-lineinfo", "--expt-relaxed-constexpr"] + COMMON
 
-SOURCES = ["kernels.cu", "combine.cu", "noalloc.cu", "exec.cpp", "graph.cpp", "plan.cpp", "arena.cpp", "api.cpp",
-           "serve.cpp", "estimate.cpp"]
-HEADERS = ["kernels.cuh", "wideint.cuh", "runtime.h", "plan.h"]
+SOURCES = ["kernels.cu", "fused.cu", "combine.cu", "noalloc.cu", "exec.cpp", "graph.cpp", "plan.cpp", "arena.cpp",
+           "api.cpp", "serve.cpp", "estimate.cpp"]
+HEADERS = ["kernels.cuh", "gather.cuh", "wideint.cuh", "runtime.h", "plan.h"]
 
 
 def _obj(src: str) -> str:

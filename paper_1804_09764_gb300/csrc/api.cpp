@@ -301,9 +301,22 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->n_active = git->second->n_act;
     out->n_directed_edges = git->second->nnz;
     if (tit->second->k == 1 || git->second->n_act == 0) return CC_OK;
-    std::unique_ptr<PlanInstance> p;
-    int n_iter = c->opt.batch > 0 ? c->opt.batch : 16;
-    CC_TRY(make_plan(c, g, t, n_iter, c->opt.width_bits, c->stream, &p));
+    // the plan the last count of (g, t) used, if it is still cached; else a
+    // plan for a count of opt.batch (or 16) colourings
+    const PlanInstance *cached = nullptr;
+    uint64_t last = 0;
+    for (auto &kv : c->plan_cache)
+        if (std::get<0>(kv.first) == g && std::get<1>(kv.first) == t && std::get<3>(kv.first) == c->opt.width_bits &&
+            kv.second.last_use >= last) {
+            cached = kv.second.p.get();
+            last = kv.second.last_use;
+        }
+    std::unique_ptr<PlanInstance> own;
+    if (!cached) {
+        int n_iter = c->opt.batch > 0 ? c->opt.batch : 16;
+        CC_TRY(make_plan(c, g, t, n_iter, c->opt.width_bits, c->stream, &own));
+    }
+    const PlanInstance *p = cached ? cached : own.get();
     out->root = p->tp.root;
     out->n_chains = (int)p->tp.chains.size();
     out->n_tables = out->n_chains - 1;
@@ -318,7 +331,7 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->table4_memory = p->tp.table4_memory;
     out->table4_computation = p->tp.table4_computation;
     out->limb_products_per_colouring = p->limb_products;
-    free_plan(c, p.get());
+    if (own) free_plan(c, own.get());
     return CC_OK;
 }
 

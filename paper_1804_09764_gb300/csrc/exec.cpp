@@ -795,7 +795,9 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     // rows of vertex v stay at (v - v0) * stride: shift the outputs by vmid - v0
                     LeafChain lt = lc;
                     for (int j = 0; j < lt.n; j++) lt.out[j] += (vmid - v0) * lt.vs[j];
-                    launch_gather_select_chain(st, Ls, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
+                    // the fused step at its own width (at most one limb below the chain's)
+                    const int Lf = std::max(L - 1, std::min(L, p->step_L[ci][0]));
+                    launch_gather_select_chain(st, Ls, Lf, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
                                                Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col,
                                                out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt, hist,
                                                next_counter());

@@ -1,0 +1,165 @@
+// gather.cuh -- device and launch helpers shared by the gather kernels
+// (kernels.cu) and the fused gather + combine kernels (fused.cu).  Internal to
+// the library: everything is in an unnamed namespace, one copy per file.
+#pragma once
+
+#include "kernels.cuh"
+#include "wideint.cuh"
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+namespace cc {
+
+namespace {
+
+constexpr int kWarps = 8;  // warps per CTA for warp-per-row kernels
+
+// Bulk prefetch of a contiguous range into L2 (no registers, no completion
+// tracking): the row of a neighbour is requested whole as soon as its id is
+// known, so the chunked loads that follow mostly hit L2.  Range and address
+// are multiples of 16 bytes (rows have an even number of 8-byte limbs).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1):
+// neighbour ids are fetched 32 at a time and broadcast with shuffles, and NB
+// neighbours' values are loaded before any is added (NB * VPT loads in flight
+// per lane).
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                                const uint64_t *__restrict__ X, int64_t R, int64_t base,
+                                                Wide<Ld> (&acc)[VPT], int lane)
+{
+    for (int64_t e = e0; e < e1; e += 32) {
+        const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+        const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+        int t = 0;
+        for (; t + NB <= cnt; t += NB) {
+            Wide<Ld> x[NB][VPT];
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                const int64_t u = __shfl_sync(0xffffffffu, myu, t + j);
+                const uint64_t *row = X + u * R * Ls;
+#pragma unroll
+                for (int q = 0; q < VPT; q++) {
+                    const int64_t c = base + q * 32 + lane;
+                    if (c < R)
+                        x[j][q] = wload<Ls, Ld>(row + c * Ls);
+                    else
+                        wzero(x[j][q]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NB; j++)
+#pragma unroll
+                for (int q = 0; q < VPT; q++) wadd(acc[q], x[j][q]);
+        }
+        for (; t < cnt; t++) {
+            const int64_t u = __shfl_sync(0xffffffffu, myu, t);
+            const uint64_t *row = X + u * R * Ls;
+#pragma unroll
+            for (int q = 0; q < VPT; q++) {
+                const int64_t c = base + q * 32 + lane;
+                if (c < R) wadd(acc[q], wload<Ls, Ld>(row + c * Ls));
+            }
+        }
+    }
+}
+
+// Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.
+// Lane `lane` owns values base + q*32 + lane, q < VPT; the neighbour ids are
+// fetched 32 at a time and broadcast with shuffles; two neighbours are loaded
+// before adding so 2*VPT loads are in flight per lane.
+template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
+__device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                           const uint64_t *__restrict__ X, int64_t R,
+                                           uint64_t *__restrict__ out_row, int lane)
+{
+    for (int64_t base = 0; base < R; base += 32 * VPT) {
+        Wide<Ld> acc[VPT];
+#pragma unroll
+        for (int q = 0; q < VPT; q++) wzero(acc[q]);
+        if (PF && base == 0 && R > 32 * VPT && (R * Ls) % 2 == 0)
+            for (int64_t e = e0 + lane; e < e1; e += 32)
+                prefetch_l2(X + (int64_t)col_idx[e] * R * Ls, (uint32_t)(R * Ls * 8));
+        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const int64_t c = base + q * 32 + lane;
+            if (c < R) wstore(out_row + c * Ld, acc[q]);
+        }
+    }
+}
+
+// Values [b0, b1) of the sum of rows X[u] over col_idx[e0, e1) into out_row
+// (b0 a multiple of 32 * VPT; b1 <= R).
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void gather_row_range(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                                 const uint64_t *__restrict__ X, int64_t R, int64_t b0, int64_t b1,
+                                                 uint64_t *__restrict__ out_row, int lane)
+{
+    for (int64_t base = b0; base < b1; base += 32 * VPT) {
+        Wide<Ld> acc[VPT];
+#pragma unroll
+        for (int q = 0; q < VPT; q++) wzero(acc[q]);
+        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const int64_t c = base + q * 32 + lane;
+            if (c < b1) wstore(out_row + c * Ld, acc[q]);
+        }
+    }
+}
+
+// Width of one of nch column segments of a row of R values: a multiple of the
+// 32 * VPT values a warp covers per sweep.
+template <int VPT>
+__device__ __forceinline__ int64_t segment_width(int64_t R, int nch)
+{
+    const int64_t per = (R + nch - 1) / nch;
+    return (per + 32 * VPT - 1) / (32 * VPT) * (32 * VPT);
+}
+
+inline unsigned grid_for(int64_t items, int per_cta) { return (unsigned)((items + per_cta - 1) / per_cta); }
+
+inline unsigned grid_stride_ctas(int64_t items, int threads)
+{
+    int64_t g = (items + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+// persistent grid size: resident CTAs per SM x SMs (queried once per kernel)
+template <typename K>
+unsigned persistent_ctas(K kernel)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;  // (kernel, device) -> CTAs
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(reinterpret_cast<const void *>(kernel), dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return (unsigned)it->second;
+    int per_sm = 1, sms = 152;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n = std::max(1, per_sm) * sms;
+    cache[key] = n;
+    return (unsigned)n;
+}
+
+#define CC_DISPATCH_L(L, ...)                  \
+    switch (L) {                               \
+    case 1: { constexpr int LL = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int LL = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int LL = 3; __VA_ARGS__; } break; \
+    default: { constexpr int LL = 4; __VA_ARGS__; } break; \
+    }
+
+}  // namespace
+
+}  // namespace cc

@@ -10,18 +10,11 @@
 //   combine_*     Eq. 1's sum over disjoint colour sets S1 u S2 = S
 //   root_reduce   Eq. 3's sum over v
 // All arithmetic is on unsigned integers modulo 2^(64 L).
-#include "kernels.cuh"
-#include "wideint.cuh"
-
-#include <algorithm>
-#include <map>
-#include <mutex>
+#include "gather.cuh"
 
 namespace cc {
 
 namespace {
-
-constexpr int kWarps = 8;  // warps per CTA for warp-per-row kernels
 
 __device__ __forceinline__ uint64_t splitmix64_out(uint64_t state)
 {
@@ -67,85 +60,6 @@ __global__ void hist_kernel(int64_t v0, int64_t v1, int B, int k, const int64_t 
     if (live) {
         uint32_t *out = hist + v * (int64_t)B * k;
         for (int i = lane; i < B * k; i += 32) out[i] = cnt[i];
-    }
-}
-
-// Bulk prefetch of a contiguous range into L2 (no registers, no completion
-// tracking): the row of a neighbour is requested whole as soon as its id is
-// known, so the chunked loads that follow mostly hit L2.  Range and address
-// are multiples of 16 bytes (rows have an even number of 8-byte limbs).
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1):
-// neighbour ids are fetched 32 at a time and broadcast with shuffles, and NB
-// neighbours' values are loaded before any is added (NB * VPT loads in flight
-// per lane).
-template <int Ls, int Ld, int VPT, int NB>
-__device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
-                                                const uint64_t *__restrict__ X, int64_t R, int64_t base,
-                                                Wide<Ld> (&acc)[VPT], int lane)
-{
-    for (int64_t e = e0; e < e1; e += 32) {
-        const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
-        const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
-        int t = 0;
-        for (; t + NB <= cnt; t += NB) {
-            Wide<Ld> x[NB][VPT];
-#pragma unroll
-            for (int j = 0; j < NB; j++) {
-                const int64_t u = __shfl_sync(0xffffffffu, myu, t + j);
-                const uint64_t *row = X + u * R * Ls;
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    const int64_t c = base + q * 32 + lane;
-                    if (c < R)
-                        x[j][q] = wload<Ls, Ld>(row + c * Ls);
-                    else
-                        wzero(x[j][q]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NB; j++)
-#pragma unroll
-                for (int q = 0; q < VPT; q++) wadd(acc[q], x[j][q]);
-        }
-        for (; t < cnt; t++) {
-            const int64_t u = __shfl_sync(0xffffffffu, myu, t);
-            const uint64_t *row = X + u * R * Ls;
-#pragma unroll
-            for (int q = 0; q < VPT; q++) {
-                const int64_t c = base + q * 32 + lane;
-                if (c < R) wadd(acc[q], wload<Ls, Ld>(row + c * Ls));
-            }
-        }
-    }
-}
-
-// Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.
-// Lane `lane` owns values base + q*32 + lane, q < VPT; the neighbour ids are
-// fetched 32 at a time and broadcast with shuffles; two neighbours are loaded
-// before adding so 2*VPT loads are in flight per lane.
-template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
-__device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
-                                           const uint64_t *__restrict__ X, int64_t R,
-                                           uint64_t *__restrict__ out_row, int lane)
-{
-    for (int64_t base = 0; base < R; base += 32 * VPT) {
-        Wide<Ld> acc[VPT];
-#pragma unroll
-        for (int q = 0; q < VPT; q++) wzero(acc[q]);
-        if (PF && base == 0 && R > 32 * VPT && (R * Ls) % 2 == 0)
-            for (int64_t e = e0 + lane; e < e1; e += 32)
-                prefetch_l2(X + (int64_t)col_idx[e] * R * Ls, (uint32_t)(R * Ls * 8));
-        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-#pragma unroll
-        for (int q = 0; q < VPT; q++) {
-            const int64_t c = base + q * 32 + lane;
-            if (c < R) wstore(out_row + c * Ld, acc[q]);
-        }
     }
 }
 
@@ -611,13 +525,6 @@ gather_group_kernel(int64_t a, int64_t b, int G, int tasks, int64_t split, const
 // pass); otherwise the grid is persistent and each warp pulls its next item
 // from the counter, so a warp that finishes a short neighbour list starts the
 // next item at once instead of idling until its CTA's longest list is done.
-template <int VPT>
-__device__ __forceinline__ int64_t segment_width(int64_t R, int nch);
-template <int Ls, int Ld, int VPT, int NB>
-__device__ __forceinline__ void gather_row_range(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
-                                                 const uint64_t *__restrict__ X, int64_t R, int64_t b0, int64_t b1,
-                                                 uint64_t *__restrict__ out_row, int lane);
-
 // Persistent mode (next != nullptr): work items are (column segment, group of
 // G consecutive vertices), segment-major: item i is segment i / ngroups of
 // group i % ngroups.  Warps in flight then read the same segment of their
@@ -658,35 +565,6 @@ gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__rest
     }
 }
 
-// Values [b0, b1) of the sum of rows X[u] over col_idx[e0, e1) into out_row
-// (b0 a multiple of 32 * VPT; b1 <= R).
-template <int Ls, int Ld, int VPT, int NB>
-__device__ __forceinline__ void gather_row_range(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
-                                                 const uint64_t *__restrict__ X, int64_t R, int64_t b0, int64_t b1,
-                                                 uint64_t *__restrict__ out_row, int lane)
-{
-    for (int64_t base = b0; base < b1; base += 32 * VPT) {
-        Wide<Ld> acc[VPT];
-#pragma unroll
-        for (int q = 0; q < VPT; q++) wzero(acc[q]);
-        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-#pragma unroll
-        for (int q = 0; q < VPT; q++) {
-            const int64_t c = base + q * 32 + lane;
-            if (c < b1) wstore(out_row + c * Ld, acc[q]);
-        }
-    }
-}
-
-// Width of one of nch column segments of a row of R values: a multiple of the
-// 32 * VPT values a warp covers per sweep.
-template <int VPT>
-__device__ __forceinline__ int64_t segment_width(int64_t R, int nch)
-{
-    const int64_t per = (R + nch - 1) / nch;
-    return (per + 32 * VPT - 1) / (32 * VPT) * (32 * VPT);
-}
-
 // Persistent mode (next != nullptr) runs items i in [0, nch * (t1 - t0)):
 // segment i / (t1 - t0) of task t0 + i % (t1 - t0), segment-major, so the
 // warps in flight read the same column segment of their neighbour rows and the
@@ -718,181 +596,6 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
         else
             gather_row_range<Ls, Ld, VPT, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, seg * cw,
                                               min(R, (seg + 1) * cw), partial + (t - t0) * R * Ld, lane);
-    }
-}
-
-// Fused gather + a = 1 combine (Eq. 1 with T_i' a single vertex): the sum of
-// the neighbour rows agg[T] goes straight to out[T u {col(v)}] (skipped when
-// col(v) is in T); entries S of the output with col(v) not in S are zero.  The
-// aggregate never reaches memory.  Persistent warps pull light vertices from
-// `next`; heavy vertices are left to the task path.
-template <int Ls, int Ld, int VPT, int NB = 2>
-__global__ void __launch_bounds__(kWarps * 32)
-gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
-                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
-                     int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
-                     const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col,
-                     uint64_t *__restrict__ out, int64_t out_vs, unsigned long long *next, int nch, int G)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t R = (int64_t)B * Cps;
-    const int64_t ngrp = (v1 - v0 + G - 1) / G, cw = segment_width<VPT>(R, nch);
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t i = (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (i >= ngrp * nch) return;
-        const int64_t seg = i / ngrp, grp = i - seg * ngrp;
-        const int64_t va = v0 + grp * G, vb = min(v1, va + G);
-        for (int64_t v = va; v < vb; v++) {
-            const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-            if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select
-            uint64_t *orow = out + (v - v0) * out_vs;
-            const uint8_t *cv = col + v * B;
-            // zeros where the vertex's colour is not in S (and in the padding):
-            // written by segment 0 only; no segment scatters to these entries
-            if (seg == 0)
-                for (int64_t i2 = lane; i2 < (int64_t)B * Chs; i2 += 32) {
-                    const int64_t b = i2 / Chs, S = i2 - b * Chs;
-                    if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
-                        Wide<Ld> z;
-                        wzero(z);
-                        wstore(orow + i2 * Ld, z);
-                    }
-                }
-            const int64_t b1 = min(R, (seg + 1) * cw);
-            for (int64_t base = seg * cw; base < b1; base += 32 * VPT) {
-                Wide<Ld> acc[VPT];
-#pragma unroll
-                for (int q = 0; q < VPT; q++) wzero(acc[q]);
-                accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-                // scatter: agg column T of colouring b lands on T u {col}
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    const int64_t c = base + q * 32 + lane;
-                    if (c < b1) {
-                        const int64_t b = c / Cps, T = c - b * Cps;
-                        if (T < Cp) {
-                            const uint32_t d = add_p[T * k + cv[b]];
-                            if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Ld, acc[q]);
-                        }
-                    }
-                }
-            }
-        }
-    }
-}
-
-// The chain's p = 1 steps for vertex v, from its first-step row orow (stride
-// Chs per colouring): out_j[S] = sum over c in S of out_{j-1}[S \ {c}] * hist[v][c].
-// The warp reads in step j the rows its lanes wrote in step j - 1 (__syncwarp).
-template <int Ld>
-__device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t *orow, int64_t Chs,
-                                           const LeafChain &chain, const uint32_t *__restrict__ hist, int B, int k,
-                                           int lane)
-{
-    const uint64_t *prev = orow;
-    int64_t prev_s = Chs;
-    const uint32_t *hr = hist + v * (int64_t)B * k;
-    for (int j = 0; j < chain.n; j++) {
-        __syncwarp();
-        const int64_t cj = chain.Ch[j], csj = chain.Chs[j];
-        const int hj = chain.h[j];
-        const uint32_t *pt = chain.pairs[j];
-        uint64_t *dst = chain.out[j] + (v - v0) * chain.vs[j];
-        for (int64_t i = lane; i < (int64_t)B * csj; i += 32) {
-            const int64_t b = i / csj, S = i - b * csj;
-            Wide<Ld> acc;
-            wzero(acc);
-            if (S < cj) {
-                const uint64_t *ar = prev + b * prev_s * Ld;
-                const uint32_t *hb = hr + b * k;
-                for (int q = 0; q < hj; q++) {
-                    const uint32_t pq = __ldg(pt + q * cj + S);
-                    const uint32_t hc = hb[pq >> 16];
-                    if (hc) {
-                        Wide<Ld> a;
-#pragma unroll
-                        for (int l = 0; l < Ld; l++) a.w[l] = ar[(pq & 0xFFFFu) * Ld + l];
-                        wmac_small(acc, a, hc);
-                    }
-                }
-            }
-            wstore(dst + i * Ld, acc);
-        }
-        prev = dst;
-        prev_s = csj;
-    }
-}
-
-// Fused gather + a = 1 combine followed, in the same warp, by the chain's p = 1
-// steps for that vertex (see LeafChain).  The rows a warp writes are the rows
-// it reads next; __syncwarp orders them within the warp.
-template <int Ls, int Ld, int VPT, int NB>
-__global__ void __launch_bounds__(kWarps * 32)
-gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
-                           const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
-                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
-                           const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col, uint64_t *out,
-                           int64_t out_vs, LeafChain chain, const uint32_t *__restrict__ hist,
-                           unsigned long long *next)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t R = (int64_t)B * Cps;
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (v >= v1) return;
-        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-        if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select, p = 1 kernels
-        uint64_t *orow = out + (v - v0) * out_vs;
-        const uint8_t *cv = col + v * B;
-        for (int64_t i = lane; i < (int64_t)B * Chs; i += 32) {
-            const int64_t b = i / Chs, S = i - b * Chs;
-            if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
-                Wide<Ld> z;
-                wzero(z);
-                wstore(orow + i * Ld, z);
-            }
-        }
-        for (int64_t base = 0; base < R; base += 32 * VPT) {
-            Wide<Ld> acc[VPT];
-#pragma unroll
-            for (int q = 0; q < VPT; q++) wzero(acc[q]);
-            accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-#pragma unroll
-            for (int q = 0; q < VPT; q++) {
-                const int64_t c = base + q * 32 + lane;
-                if (c < R) {
-                    const int64_t b = c / Cps, T = c - b * Cps;
-                    if (T < Cp) {
-                        const uint32_t d = add_p[T * k + cv[b]];
-                        if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Ld, acc[q]);
-                    }
-                }
-            }
-        }
-        leaf_steps<Ld>(v, v0, orow, Chs, chain, hist, B, k, lane);
-    }
-}
-
-// The chain's p = 1 steps for light vertices whose first-step rows were
-// written by a previous kernel (rows of vertex v at out0 + (v - v0) * out_vs).
-template <int Ld>
-__global__ void __launch_bounds__(kWarps * 32)
-leaf_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr, int B, int k,
-                  const uint64_t *out0, int64_t out_vs, int64_t Chs, LeafChain chain,
-                  const uint32_t *__restrict__ hist, unsigned long long *next)
-{
-    const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (v >= v1) return;
-        if (row_ptr[v + 1] - row_ptr[v] > split) continue;  // heavy: the p = 1 kernels
-        leaf_steps<Ld>(v, v0, out0 + (v - v0) * out_vs, Chs, chain, hist, B, k, lane);
     }
 }
 
@@ -1137,34 +840,6 @@ __global__ void permute_lists_kernel(int64_t n_act, int64_t n, const int64_t *__
     }
 }
 
-inline unsigned grid_for(int64_t items, int per_cta) { return (unsigned)((items + per_cta - 1) / per_cta); }
-
-inline unsigned grid_stride_ctas(int64_t items, int threads)
-{
-    int64_t g = (items + threads - 1) / threads;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
-}
-
-// persistent grid size: resident CTAs per SM x SMs (queried once per kernel)
-template <typename K>
-unsigned persistent_ctas(K kernel)
-{
-    static std::mutex mu;
-    static std::map<std::pair<const void *, int>, int> cache;  // (kernel, device) -> CTAs
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(reinterpret_cast<const void *>(kernel), dev);
-    auto it = cache.find(key);
-    if (it != cache.end()) return (unsigned)it->second;
-    int per_sm = 1, sms = 152;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int n = std::max(1, per_sm) * sms;
-    cache[key] = n;
-    return (unsigned)n;
-}
-
 template <int Ls, int Ld>
 void gather_light_t(cudaStream_t st, bool pf, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                     const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg, unsigned long long *next, int nch,
@@ -1191,14 +866,6 @@ void gather_tasks_t(cudaStream_t st, bool pf, int nb, int64_t t0, int64_t t1, co
     const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(items, kWarps)) : grid_for(t1 - t0, kWarps);
     k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next, nch);
 }
-
-#define CC_DISPATCH_L(L, ...)                  \
-    switch (L) {                               \
-    case 1: { constexpr int LL = 1; __VA_ARGS__; } break; \
-    case 2: { constexpr int LL = 2; __VA_ARGS__; } break; \
-    case 3: { constexpr int LL = 3; __VA_ARGS__; } break; \
-    default: { constexpr int LL = 4; __VA_ARGS__; } break; \
-    }
 
 }  // namespace
 
@@ -1450,86 +1117,6 @@ void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int 
     default: break;
     }
 #undef CC_CH
-}
-
-namespace {
-
-template <int Ls, int Ld>
-void gather_select_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
-                     const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
-                     int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col, uint64_t *out,
-                     unsigned long long *next, int nch, int G, int64_t out_vs)
-{
-    constexpr int VPT = Ld <= 2 ? 4 : 2;
-    auto kfn = nb == 4 ? gather_select_kernel<Ls, Ld, VPT, 4> : gather_select_kernel<Ls, Ld, VPT, 2>;
-    const int64_t items = (v1 - v0 + G - 1) / G * nch;
-    const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(items, kWarps));
-    kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
-                                   out_vs > 0 ? out_vs : (int64_t)B * Chs * Ld, next, nch, G);
-}
-
-}  // namespace
-
-void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
-                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
-                          int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
-                          const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next, int nb,
-                          int nch, int G, int64_t out_vs)
-{
-    if (v1 <= v0) return;
-    nch = std::max(1, std::min(nch, 64));
-    G = std::max(1, G);
-#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next, nch, G, out_vs)
-    CC_GS(1, 1); CC_GS(1, 2); CC_GS(1, 3); CC_GS(1, 4);
-    CC_GS(2, 1); CC_GS(2, 2); CC_GS(2, 3); CC_GS(2, 4);
-    CC_GS(3, 1); CC_GS(3, 2); CC_GS(3, 3); CC_GS(3, 4);
-    CC_GS(4, 1); CC_GS(4, 2); CC_GS(4, 3); CC_GS(4, 4);
-#undef CC_GS
-}
-
-namespace {
-
-template <int Ls, int Ld>
-void gather_select_chain_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
-                           const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
-                           int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col,
-                           uint64_t *out, int64_t out_vs, const LeafChain &chain, const uint32_t *hist,
-                           unsigned long long *next)
-{
-    constexpr int VPT = Ld <= 2 ? 4 : 2;
-    auto kfn = nb == 4 ? gather_select_chain_kernel<Ls, Ld, VPT, 4> : gather_select_chain_kernel<Ls, Ld, VPT, 2>;
-    const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
-    kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
-                                   out_vs, chain, hist, next);
-}
-
-}  // namespace
-
-void launch_gather_select_chain(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
-                                const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
-                                int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
-                                const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
-                                const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb)
-{
-    if (v1 <= v0) return;
-#define CC_GC(a, b) if (Ls == a && Ld == b) return gather_select_chain_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, hist, next)
-    CC_GC(1, 1); CC_GC(1, 2); CC_GC(1, 3); CC_GC(1, 4);
-    CC_GC(2, 1); CC_GC(2, 2); CC_GC(2, 3); CC_GC(2, 4);
-    CC_GC(3, 1); CC_GC(3, 2); CC_GC(3, 3); CC_GC(3, 4);
-    CC_GC(4, 1); CC_GC(4, 2); CC_GC(4, 3); CC_GC(4, 4);
-#undef CC_GC
-}
-
-void launch_leaf_chain(cudaStream_t st, int Ld, int64_t v0, int64_t v1, int64_t split, const int64_t *row_ptr, int B,
-                       int k, const uint64_t *out0, int64_t out_vs, int64_t Chs, const LeafChain &chain,
-                       const uint32_t *hist, unsigned long long *next)
-{
-    if (v1 <= v0 || chain.n <= 0) return;
-    CC_DISPATCH_L(Ld, {
-        auto kfn = leaf_chain_kernel<LL>;
-        const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
-        kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, row_ptr, B, k, out0, out_vs, Chs, chain, hist, next);
-    });
 }
 
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,

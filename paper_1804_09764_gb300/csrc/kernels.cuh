@@ -134,7 +134,8 @@ struct LeafChain {
     const uint32_t *pairs[15];   // (h, h-1) split tables
     uint64_t *out[15];
 };
-void launch_gather_select_chain(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
+// Lf: limbs of the fused step's sums and rows (Ld or Ld - 1); Ld: the leaf steps'
+void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t v0, int64_t v1, int64_t split,
                                 const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
