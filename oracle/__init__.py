@@ -51,10 +51,12 @@ def _load():
         lib = ctypes.CDLL(_LIB_PATH)
         P = ctypes.c_void_p
         lib.cco_count.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, P, ctypes.c_int,
-                                  ctypes.c_uint64, ctypes.c_uint64, P, P]
+                                  ctypes.c_uint64, ctypes.c_uint64, P, P, P, P]
         lib.cco_count.restype = ctypes.c_int
         lib.cco_automorphisms.argtypes = [ctypes.c_int, P]
         lib.cco_automorphisms.restype = ctypes.c_int64
+        lib.cco_automorphisms_labelled.argtypes = [ctypes.c_int, P, P]
+        lib.cco_automorphisms_labelled.restype = ctypes.c_int64
         lib.cco_colour.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
         lib.cco_colour.restype = ctypes.c_int
         lib.cco_splitmix64.argtypes = [ctypes.c_uint64]
@@ -85,9 +87,14 @@ def _edges_array(k, edges):
     return np.ascontiguousarray(e) if e.size else np.zeros(2, dtype=np.int32)
 
 
-def automorphisms(k: int, edges) -> int:
-    """|Aut(T)| by backtracking over bijections of V_T."""
-    r = _load().cco_automorphisms(k, _ptr(_edges_array(k, edges)))
+def automorphisms(k: int, edges, labels=None) -> int:
+    """|Aut(T)| by backtracking over bijections of V_T (with labels: only the
+    label-preserving ones)."""
+    if labels is not None:
+        lab = np.ascontiguousarray(labels, dtype=np.uint8)
+        r = _load().cco_automorphisms_labelled(k, _ptr(_edges_array(k, edges)), _ptr(lab))
+    else:
+        r = _load().cco_automorphisms(k, _ptr(_edges_array(k, edges)))
     if r < 0:
         raise ValueError("template is not a tree")
     return int(r)
@@ -117,8 +124,10 @@ def u256_add(a: int, b: int) -> int:
 
 
 def count_maps(graph, k: int, edges, root: int = 0, seed: int = 0, j: int = 0,
-               colours=None, ids=None, per_vertex: bool = False):
-    """Labelled colourful maps for colouring j (mod 2^256).
+               colours=None, ids=None, per_vertex: bool = False, glabels=None, tlabels=None):
+    """Colourful maps (injective homomorphisms V_T -> V_G whose images have k
+    distinct colours) for colouring j, mod 2^256.  With vertex labels glabels
+    [n] and tlabels [k] (both or neither) only label-preserving maps count.
 
     Returns ``maps`` or ``(maps, per_vertex_list)``.
     """
@@ -132,8 +141,13 @@ def count_maps(graph, k: int, edges, root: int = 0, seed: int = 0, j: int = 0,
     idv = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
     tot = np.zeros(4, dtype=np.uint64)
     pv = np.zeros((max(n, 1), 4), dtype=np.uint64) if per_vertex else None
+    gl = None if glabels is None else np.ascontiguousarray(glabels, dtype=np.uint8)
+    tl = None if tlabels is None else np.ascontiguousarray(tlabels, dtype=np.uint8)
+    if (gl is None) != (tl is None) or (gl is not None and (gl.size != n or tl.size != k)):
+        raise ValueError("give graph and template labels together, one per vertex")
     rc = lib.cco_count(n, _ptr(rp), _ptr(ci), _ptr(idv), _ptr(col), k,
-                       _ptr(_edges_array(k, edges)), root, seed & (2**64 - 1), j, _ptr(tot), _ptr(pv))
+                       _ptr(_edges_array(k, edges)), root, seed & (2**64 - 1), j, _ptr(tot), _ptr(pv),
+                       _ptr(gl), _ptr(tl))
     if rc != 0:
         raise RuntimeError(f"oracle failed: {rc}")
     maps = _limbs_to_int(tot)

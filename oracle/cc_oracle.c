@@ -164,7 +164,9 @@ static int is_adj(const tmpl_t *t, int a, int b)
     return 0;
 }
 
-static int64_t aut_rec(const tmpl_t *t, const int *order, const int *par, int i,
+/* lab (optional): vertex labels; an automorphism must then map every vertex
+ * to one with the same label. */
+static int64_t aut_rec(const tmpl_t *t, const uint8_t *lab, const int *order, const int *par, int i,
                        int *img, int *used)
 {
     if (i == t->k) return 1;
@@ -172,15 +174,16 @@ static int64_t aut_rec(const tmpl_t *t, const int *order, const int *par, int i,
     int64_t total = 0;
     for (int y = 0; y < t->k; y++) {
         if (used[y] || t->nadj[y] != t->nadj[x]) continue;
+        if (lab && lab[y] != lab[x]) continue;
         if (par[x] >= 0 && !is_adj(t, img[par[x]], y)) continue;
         used[y] = 1; img[x] = y;
-        total += aut_rec(t, order, par, i + 1, img, used);
+        total += aut_rec(t, lab, order, par, i + 1, img, used);
         used[y] = 0;
     }
     return total;
 }
 
-int64_t cco_automorphisms(int k, const int32_t *edges)
+static int64_t automorphisms(int k, const int32_t *edges, const uint8_t *labels)
 {
     tmpl_t t;
     if (tmpl_build(&t, k, edges)) return -1;
@@ -194,7 +197,15 @@ int64_t cco_automorphisms(int k, const int32_t *edges)
         }
     }
     int img[MAXK], used[MAXK] = {0};
-    return aut_rec(&t, order, par, 0, img, used);
+    return aut_rec(&t, labels, order, par, 0, img, used);
+}
+
+int64_t cco_automorphisms(int k, const int32_t *edges) { return automorphisms(k, edges, NULL); }
+
+/* Label-preserving automorphisms of a vertex-labelled tree. */
+int64_t cco_automorphisms_labelled(int k, const int32_t *edges, const uint8_t *labels)
+{
+    return labels ? automorphisms(k, edges, labels) : -1;
 }
 
 /* ---------------------------------------------------------------- colour sets */
@@ -246,6 +257,8 @@ typedef struct {
     const int64_t *row_ptr;
     const int32_t *col_idx;
     const uint8_t *col;     /* colour of each vertex */
+    const uint8_t *glab;    /* vertex labels of the graph and of the template */
+    const uint8_t *tlab;    /*   (both NULL: unlabelled) */
     tmpl_t t;
     sets_t sets;
     int children[MAXK][MAXK];
@@ -284,12 +297,14 @@ static void root_tree(dp_t *d, int x, int parent)
  */
 static u256 *subtree_table(dp_t *d, int x)
 {
-    /* base case: M(v, {x}, {c}) = [col(v) == c] */
+    /* base case: M(v, {x}, {c}) = [col(v) == c], times [label(v) == label(x)]
+       for labelled counts (a map must preserve labels) */
     u256 *cur = table_alloc(d, 1);
     if (!cur) return NULL;
     const int c1 = d->sets.count[1];
     for (int64_t v = 0; v < d->n; v++)
-        cur[(size_t)v * c1 + d->sets.index_of[1 << d->col[v]]].w[0] = 1;
+        if (!d->glab || d->glab[v] == d->tlab[x])
+            cur[(size_t)v * c1 + d->sets.index_of[1 << d->col[v]]].w[0] = 1;
     int cur_size = 1;
 
     for (int ci = 0; ci < d->nchildren[x]; ci++) {
@@ -357,19 +372,26 @@ static u256 *subtree_table(dp_t *d, int x)
  *   k, edges[2(k-1)]: the tree template; root: its root vertex.
  *   total[4]: sum_v M(v, T, all colours), mod 2^256.
  *   per_vertex: optional [n][4], M(v, T, all colours) for every v.
- * Returns 0, -1 for a bad template or root, -2 for an out-of-range colour,
- * -3 if memory ran out.
+ *   glabels[n], tlabels[k]: optional vertex labels of the graph and the
+ *        template (both or neither); a counted map then sends every template
+ *        vertex to a graph vertex with the same label.
+ * Returns 0, -1 for a bad template, root or label pair, -2 for an
+ * out-of-range colour, -3 if memory ran out.
  */
 int cco_count(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
               const int64_t *ids, const uint8_t *colours,
               int k, const int32_t *edges, int root,
               uint64_t seed, uint64_t j,
-              uint64_t *total, uint64_t *per_vertex)
+              uint64_t *total, uint64_t *per_vertex,
+              const uint8_t *glabels, const uint8_t *tlabels)
 {
     dp_t d;
     memset(&d, 0, sizeof d);
     if (tmpl_build(&d.t, k, edges)) return -1;
     if (root < 0 || root >= k) return -1;
+    if (!glabels != !tlabels) return -1;
+    d.glab = glabels;
+    d.tlab = tlabels;
     d.n = n; d.row_ptr = row_ptr; d.col_idx = col_idx;
     uint8_t *col = (uint8_t *)malloc(n ? (size_t)n : 1);
     if (!col) return -3;

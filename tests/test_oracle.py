@@ -284,3 +284,62 @@ def test_unbiasedness_over_all_colourings_small():
     ests = [O.estimate(O.count_maps(g, k, edges, 1, colours=np.array(c, dtype=np.uint8)) // aut, k)
             for c in itertools.product(range(k), repeat=n)]
     assert math.fsum(ests) / len(ests) == pytest.approx(brute_copies_uncoloured(g, k, edges), rel=1e-12)
+
+
+# ----------------------------------------------------------------- labelled templates
+# Vertex labels on G and T: a counted map sends every template vertex to a
+# graph vertex with the same label (the labelled templates of SAHAD, cited in
+# the related work); copies divide by the label-preserving automorphisms.
+
+def brute_maps_labelled(graph, colours, k, edges, glab, tlab):
+    nb = [set(graph.neighbours(v).tolist()) for v in range(graph.n)]
+    cnt = 0
+    for img in itertools.permutations(range(graph.n), k):
+        if any(glab[img[x]] != tlab[x] for x in range(k)):
+            continue
+        if len({colours[v] for v in img}) != k:
+            continue
+        if all(img[b] in nb[img[a]] for a, b in edges):
+            cnt += 1
+    return cnt
+
+
+def brute_aut_labelled(k, edges, lab):
+    E = {frozenset(e) for e in edges}
+    return sum(1 for p in itertools.permutations(range(k))
+               if all(lab[p[x]] == lab[x] for x in range(k))
+               and all(frozenset((p[a], p[b])) in E for a, b in edges))
+
+
+@pytest.mark.parametrize("name", ["P3", "P4", "star4", "spider5"])
+def test_labelled_dp_matches_brute_force_every_root(name):
+    k, edges = SMALL_TEMPLATES[name]
+    rng = random.Random(sum(map(ord, name)) * 7919)
+    g = gg.random_graph_gnp(9, 0.5, seed=31)
+    for trial in range(3):
+        colours = [rng.randrange(k) for _ in range(g.n)]
+        glab = [rng.randrange(2) for _ in range(g.n)]
+        tlab = [rng.randrange(2) for _ in range(k)]
+        bf = brute_maps_labelled(g, colours, k, edges, glab, tlab)
+        for root in range(k):
+            assert O.count_maps(g, k, edges, root, colours=colours, glabels=glab, tlabels=tlab) == bf
+
+
+def test_labelled_counts_over_all_template_labellings_sum_to_unlabelled():
+    # every map induces exactly one labelling of T (the labels of its image),
+    # so summing over all labellings of the template gives the unlabelled count
+    k, edges = SMALL_TEMPLATES["cat6"]
+    g = gg.rmat_graph(7, seed=5)
+    glab = np.random.default_rng(3).integers(0, 2, g.n)
+    total = sum(O.count_maps(g, k, edges, 1, seed=7, j=0, glabels=glab, tlabels=list(t))
+                for t in itertools.product(range(2), repeat=k))
+    assert total == O.count_maps(g, k, edges, 1, seed=7, j=0)
+
+
+def test_labelled_automorphisms_against_permutations():
+    rng = random.Random(11)
+    for name, (k, e) in SMALL_TEMPLATES.items():
+        for _ in range(4):
+            lab = [rng.randrange(2) for _ in range(k)]
+            assert O.automorphisms(k, e, lab) == brute_aut_labelled(k, e, lab)
+        assert O.automorphisms(k, e, [0] * k) == O.automorphisms(k, e)
