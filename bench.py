@@ -45,6 +45,9 @@ WORKLOADS = {
     # root 1, the planner's root for the scale-22 headline)
     "rmat18_tree12": dict(graph=("rmat", 18, 18), template="tree12", root=1, n_iter=1, budget=16 << 30),
     "rmat24_spider15": dict(graph=("rmat", 24, 24), template="spider15", root=0, n_iter=4, budget=150 << 30),
+    # labelled templates: 4 seeded labels on graph and template vertices
+    "rmat22_tree12_labelled": dict(graph=("rmat", 22, 22), template="tree12", root=-1, n_iter=16,
+                                   budget=100 << 30, labels=4),
     # small case of the spider-15 combine for profiler captures (a few GB)
     "rmat16_spider15": dict(graph=("rmat", 16, 16), template="spider15", root=0, n_iter=1, budget=6 << 30),
 }
@@ -446,7 +449,13 @@ def main():
                      block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused,
                      autotune=args.autotune, vertex_order=args.vertex_order, col_chunks=args.col_chunks)
     gid = ctx.graph_load(g)
-    tid = ctx.template_load(k, e, wl["root"])
+    tlab = glab = None
+    if wl.get("labels"):
+        rng = np.random.default_rng(1234)
+        glab = rng.integers(0, wl["labels"], g.n, dtype=np.uint8)
+        ctx.graph_set_labels(gid, glab)
+        tlab = rng.integers(0, wl["labels"], k, dtype=np.uint8)
+    tid = ctx.template_load(k, e, wl["root"], labels=tlab)
     n_iter = wl["n_iter"]
 
     def step(i):
@@ -486,12 +495,14 @@ def main():
             torch.cuda.synchronize()
             t = time.perf_counter()
             gid2 = ctx.graph_load_csr(rp, ci, g.n)
+            if glab is not None:
+                ctx.graph_set_labels(gid2, glab)
             r = ctx.count(gid2, tid, seed=777, n_iter=n_iter, first_iter=i * n_iter)
             ctx.graph_free(gid2)
             ctx2_t.append(time.perf_counter() - t)
         et = sum(ctx2_t[1:])
         e2e = {"value": info["updates_per_colouring"] * n_iter * args.steps * world / et, "unit": "updates/s",
-               "h2d_bytes_per_step": int(rp.numel() * 8 + ci.numel() * 4),
+               "h2d_bytes_per_step": int(rp.numel() * 8 + ci.numel() * 4 + (0 if glab is None else glab.size)),
                "d2h_bytes_per_step": int(n_iter * 4 * 8)}
 
     if rank != 0:
@@ -534,6 +545,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "n_active": info["n_active"],
                    "template": wl["template"], "k": k, "root": info["root"], "colourings_per_step": n_iter,
+                   "labels": wl.get("labels", 0),
                    "batch": info["batch"], "blocks": info["n_blocks"], "limbs_root": info["limbs_root"],
                    "workspace_gb": info["workspace_bytes"] / 1e9, "l2": "inputs larger than L2",
                    "updates_per_colouring": info["updates_per_colouring"],

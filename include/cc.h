@@ -135,6 +135,26 @@ cc_status cc_template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, int32_t
                            cc_template_id *out);
 cc_status cc_template_free(cc_ctx *ctx, cc_template_id t);
 
+/*
+ * Labelled templates (the extension of colour coding to vertex-labelled
+ * templates cited in the paper's related work): template vertex x carries
+ * labels[x] (k bytes, copied), and a counted map must send every template
+ * vertex to a graph vertex with the same label.  Copies divide by the
+ * label-preserving automorphisms (cc_result.aut).  Counting a labelled
+ * template needs graph labels (cc_graph_set_labels); otherwise
+ * CC_ERR_INVALID_ARG.  Errors as cc_template_load; labels NULL: invalid.
+ */
+cc_status cc_template_load_labelled(cc_ctx *ctx, int32_t k, const int32_t *edges, const uint8_t *labels,
+                                    int32_t root, cc_template_id *out);
+
+/*
+ * Vertex labels of a loaded graph: labels[v] for v in [0, n) in the numbering
+ * of cc_graph_load_csr (host array, copied; NULL removes the labels).  Used
+ * by labelled templates only; unlabelled templates ignore them.  Drops the
+ * graph's cached plans.  Errors: CC_ERR_NOT_FOUND, CC_ERR_BUDGET.
+ */
+cc_status cc_graph_set_labels(cc_ctx *ctx, cc_graph_id g, const uint8_t *labels);
+
 /* Results of a count (one per call or per request). */
 typedef struct cc_result {
     int32_t k;
@@ -395,6 +415,10 @@ cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_
 
 /* |Aut(T)| from rooted canonical forms at the tree centre.  Host only. */
 cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *aut);
+
+/* The label-preserving automorphisms of a vertex-labelled tree (labels[k]).
+ * Host only. */
+cc_status cc_template_automorphisms_labelled(int32_t k, const int32_t *edges, const uint8_t *labels, int64_t *aut);
 
 /* The rate of 64-bit limb products (a 64 x 64-bit multiply's low and high
  * halves counted as two, each with its carry-propagating add) that the

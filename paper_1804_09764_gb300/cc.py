@@ -35,6 +35,7 @@ EXPORTED = [
     "cc_poll", "cc_wait", "cc_cancel", "cc_serve_stats_get", "cc_template_cost",
     "cc_template_automorphisms", "cc_version", "cc_table_gather", "cc_table_gather_noalloc",
     "cc_iterations_for", "cc_estimate", "cc_count_multi", "cc_multi_plan_info_get", "cc_limb_product_rate",
+    "cc_template_load_labelled", "cc_graph_set_labels", "cc_template_automorphisms_labelled",
 ]
 
 
@@ -154,6 +155,9 @@ def load_library(path: str = LIB_PATH):
         "cc_count_multi": (I32, [P, I64, P, I32, P, P, I32, P]),
         "cc_multi_plan_info_get": (I32, [P, I64, P, I32, I32, P]),
         "cc_limb_product_rate": (I32, [P, P]),
+        "cc_template_load_labelled": (I32, [P, I32, P, P, I32, P]),
+        "cc_graph_set_labels": (I32, [P, I64, P]),
+        "cc_template_automorphisms_labelled": (I32, [I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -203,6 +207,17 @@ def cc_template_automorphisms(k: int, edges) -> int:
     a = ctypes.c_int64()
     e = _edges_array(k, edges)
     _check(lib.cc_template_automorphisms(k, _ptr(e), ctypes.byref(a)))
+    return a.value
+
+
+def cc_template_automorphisms_labelled(k: int, edges, labels) -> int:
+    lib = load_library()
+    a = ctypes.c_int64()
+    e = _edges_array(k, edges)
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+    if lab.size != k:
+        raise ValueError("one label per template vertex")
+    _check(lib.cc_template_automorphisms_labelled(k, _ptr(e), _ptr(lab), ctypes.byref(a)))
     return a.value
 
 
@@ -313,11 +328,26 @@ class Context:
     def graph_free(self, gid: int):
         _check(self._lib.cc_graph_free(self._h, gid))
 
-    def template_load(self, k: int, edges, root: int = -1) -> int:
+    def template_load(self, k: int, edges, root: int = -1, labels=None) -> int:
+        """cc_template_load, or cc_template_load_labelled with k vertex labels."""
         tid = ctypes.c_int64()
         e = _edges_array(k, edges)
-        _check(self._lib.cc_template_load(self._h, k, _ptr(e), root, ctypes.byref(tid)))
+        if labels is None:
+            _check(self._lib.cc_template_load(self._h, k, _ptr(e), root, ctypes.byref(tid)))
+        else:
+            lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+            if lab.size != k:
+                raise ValueError("one label per template vertex")
+            _check(self._lib.cc_template_load_labelled(self._h, k, _ptr(e), _ptr(lab), root, ctypes.byref(tid)))
         return tid.value
+
+    def graph_set_labels(self, gid: int, labels):
+        """cc_graph_set_labels: one uint8 label per vertex (None removes them)."""
+        if labels is None:
+            _check(self._lib.cc_graph_set_labels(self._h, gid, None))
+            return
+        lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+        _check(self._lib.cc_graph_set_labels(self._h, gid, _ptr(lab)))
 
     def template_free(self, tid: int):
         _check(self._lib.cc_template_free(self._h, tid))

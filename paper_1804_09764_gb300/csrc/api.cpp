@@ -179,23 +179,65 @@ cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g)
     return CC_OK;
 }
 
-cc_status cc_template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, int32_t root, cc_template_id *out)
+static cc_status template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, const uint8_t *labels, int32_t root,
+                               cc_template_id *out)
 {
     if (!ctx || !out) return fail(CC_ERR_INVALID_ARG, "ctx or out is NULL");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     TemplatePlan tp;
     std::string err;
-    int rc = build_template_plan(k, edges, root, 1, 16.0, &tp, &err);
+    int rc = build_template_plan(k, edges, root, 1, 16.0, &tp, &err, labels);
     if (rc) return fail(rc, err);
     auto t = std::make_unique<Template>();
     t->k = k;
     t->root_req = root;
     if (k > 1) t->edges.assign(edges, edges + 2 * (k - 1));
+    if (labels) t->labels.assign(labels, labels + k);
     t->aut = tp.aut;
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     int64_t id = c->next_id++;
     c->templates[id] = std::move(t);
     *out = id;
+    return CC_OK;
+}
+
+cc_status cc_template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, int32_t root, cc_template_id *out)
+{
+    return template_load(ctx, k, edges, nullptr, root, out);
+}
+
+cc_status cc_template_load_labelled(cc_ctx *ctx, int32_t k, const int32_t *edges, const uint8_t *labels,
+                                    int32_t root, cc_template_id *out)
+{
+    if (!labels) return fail(CC_ERR_INVALID_ARG, "labels is NULL");
+    return template_load(ctx, k, edges, labels, root, out);
+}
+
+cc_status cc_graph_set_labels(cc_ctx *ctx, cc_graph_id g, const uint8_t *labels)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    auto it = c->graphs.find(g);
+    if (it == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    Graph *G = it->second.get();
+    cudaSetDevice(c->device);
+    evict_plans(c, g);  // cached plans and captured passes hold the label pointer
+    c->arena.free(G->labels);
+    G->labels = nullptr;
+    G->h_labels.clear();
+    if (!labels) return CC_OK;
+    G->h_labels.assign(labels, labels + G->n);
+    std::vector<uint8_t> lc(std::max<int64_t>(G->n_act, 1), 0);
+    for (int64_t v = 0; v < G->n; v++)
+        if (G->h_new_id[v] >= 0) lc[G->h_new_id[v]] = labels[v];
+    G->labels = (uint8_t *)arena_alloc(c, lc.size());
+    if (!G->labels) {
+        G->h_labels.clear();
+        return fail(CC_ERR_BUDGET, "no room for the vertex labels");
+    }
+    CC_CUDA(cudaMemcpyAsync(G->labels, lc.data(), lc.size(), cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(cudaStreamSynchronize(c->stream));
     return CC_OK;
 }
 
@@ -377,6 +419,17 @@ cc_status cc_template_cost(int32_t k, const int32_t *edges, int32_t root, int32_
     if (rc) return fail(rc, err);
     *memory = tp.table4_memory;
     *computation = tp.table4_computation;
+    return CC_OK;
+}
+
+cc_status cc_template_automorphisms_labelled(int32_t k, const int32_t *edges, const uint8_t *labels, int64_t *aut)
+{
+    if (!aut || !labels) return fail(CC_ERR_INVALID_ARG, "aut or labels is NULL");
+    TemplatePlan tp;
+    std::string err;
+    int rc = build_template_plan(k, edges, 0, 0, 16.0, &tp, &err, labels);
+    if (rc) return fail(rc, err);
+    *aut = tp.aut;
     return CC_OK;
 }
 

@@ -253,7 +253,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
         }
     const int Lm = p.Lmax;
     Lo.off_col = take((uint64_t)n * B);
-    Lo.off_hist = need_hist ? take((uint64_t)n * B * k * 4) : 0;
+    Lo.off_hist = need_hist ? take((uint64_t)n * B * k * 4 * std::max<size_t>(1, p.hist_labels.size())) : 0;
     Lo.off_act[0] = take((uint64_t)V * B * maxAct * 8 * Lm);
     Lo.off_act[1] = take((uint64_t)V * B * maxAct * 8 * Lm);
     Lo.off_agg = take((uint64_t)V * B * maxP * 8 * Lm);
@@ -279,6 +279,9 @@ cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, 
                            TemplatePlan *tp_out, std::vector<int> *chain_L_out, int *L_root_out)
 {
     std::string err;
+    const uint8_t *labels = t->labels.empty() ? nullptr : t->labels.data();
+    if (labels && g->h_labels.empty())
+        return fail(CC_ERR_INVALID_ARG, "labelled template on a graph without vertex labels");
     double avg = g->n_act ? (double)g->nnz / g->n_act : 1.0;
     // Integer widths of a partition: every chain at the smallest L with
     // max_v H(v) < 2^(64 L), capped at the root's L (which covers sum_v H).
@@ -326,7 +329,7 @@ cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, 
         return bytes / 6.0e12 + work / 3.0e11;
     };
     if (t->root_req >= 0 || t->k <= 2 || g->n_act == 0) {
-        int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &*tp_out, &err);
+        int rc = build_template_plan(t->k, t->edges.data(), t->root_req, 1, avg, &*tp_out, &err, labels);
         if (rc) return fail(rc, err);
         CC_TRY(widths(*tp_out, chain_L_out, L_root_out));
     } else {
@@ -336,7 +339,7 @@ cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, 
         std::vector<std::pair<double, int>> rank;
         for (int r = 0; r < t->k; r++) {
             TemplatePlan tp;
-            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err);
+            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err, labels);
             if (rc) return fail(rc, err);
             rank.push_back({model(tp, std::vector<int>(tp.chains.size(), 1)), r});
         }
@@ -345,7 +348,7 @@ cc_status select_partition(Ctx *c, Graph *g, const Template *t, int width_bits, 
         for (size_t ri = 0; ri < rank.size() && rank[ri].first < best; ri++) {
             const int r = rank[ri].second;
             TemplatePlan tp;
-            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err);
+            int rc = build_template_plan(t->k, t->edges.data(), r, 1, avg, &tp, &err, labels);
             if (rc) return fail(rc, err);
             std::vector<int> cl;
             int lr = 1;
@@ -478,6 +481,12 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     const TemplatePlan &tp = p->tp;
     const int k = tp.k;
     const int nc = (int)tp.chains.size();
+    p->hist_labels.clear();
+    for (auto &C : tp.chains)
+        for (auto &s : C.steps)
+            if (s.src_chain < 0 &&
+                std::find(p->hist_labels.begin(), p->hist_labels.end(), s.leaf_label) == p->hist_labels.end())
+                p->hist_labels.push_back(s.leaf_label);
     p->width_bits = width_bits;
     p->exact = width_bits == 0;
     p->Lmax = *std::max_element(p->chain_L.begin(), p->chain_L.end());
@@ -694,12 +703,17 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     launch_colour(st, g->n_act, B, k, g->orig, (const ColourParams *)W(p->off_params), col);
     Ln.end(1, (double)g->n_act * (8 + B));
     uint32_t *hist = (uint32_t *)W(p->off_hist);
-    bool need_hist = false;
-    for (auto &C : tp.chains)
-        for (auto &s : C.steps) need_hist |= s.src_chain < 0;
-    if (need_hist) {
+    // the histogram of a leaf child with label `lab` (-1: all neighbours)
+    auto hist_for = [&](int lab) -> uint32_t * {
+        for (size_t i = 0; i < p->hist_labels.size(); i++)
+            if (p->hist_labels[i] == lab) return hist + i * (uint64_t)g->n_act * B * k;
+        return hist;
+    };
+    if (!p->hist_labels.empty()) {
         Ln.begin(K_HIST);
-        launch_hist(st, 0, g->n_act, B, k, g->row_ptr, g->col_idx, col, hist);
+        for (int lab : p->hist_labels)
+            launch_hist(st, 0, g->n_act, B, k, g->row_ptr, g->col_idx, col, hist_for(lab),
+                        lab >= 0 ? g->labels : nullptr, lab);
         Ln.end(1, (double)g->nnz * (4 + B) + (double)g->n_act * (8 + 4.0 * B * k));
     }
     for (size_t ci = 0; ci < tp.chains.size(); ci++) {
@@ -764,8 +778,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     lc.Chs[j - 1] = cs;
                     lc.vs[j - 1] = vstride(j, cs);
                     lc.pairs[j - 1] = p->d_pairs.at({C.steps[j].h, C.steps[j].a});
+                    lc.hist[j - 1] = hist_for(C.steps[j].leaf_label);
                 }
-                const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
                 const int64_t nh = hv.h1 - hv.h0;
                 // algorithmic bytes of the chain for `nvert` vertices with `edges` list entries:
                 // neighbour rows + ids + row pointers + the step rows written, and per
@@ -788,7 +802,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                          Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, next_counter(), 4, nch,
                                          vertex_group(nch), vstride(0, Chs0));
                     launch_leaf_chain(st, L, v0, vmid, p->split, g->row_ptr, B, k, out0, vstride(0, Chs0), Chs0, lc,
-                                      hist, next_counter());
+                                      next_counter());
                     nl += 2;
                 }
                 if (v1 > vmid) {
@@ -799,7 +813,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const int Lf = std::max(L - 1, std::min(L, p->step_L[ci][0]));
                     launch_gather_select_chain(st, Ls, Lf, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
                                                Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col,
-                                               out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt, hist,
+                                               out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt,
                                                next_counter());
                     nl++;
                 }
@@ -817,7 +831,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     int64_t prev_s = Chs0;
                     for (int j = 0; j < lc.n; j++) {
                         launch_combine_hist(st, L, L, nh, B, k, lc.Ch[j], lc.Chs[j], prev_s, lc.h[j], lc.pairs[j],
-                                            prev, hrow, lc.out[j]);
+                                            prev, lc.hist[j] + (uint64_t)v0 * B * k, lc.out[j]);
                         prev = lc.out[j];
                         prev_s = lc.Chs[j];
                     }
@@ -832,7 +846,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 // limbs of this step's output, of the previous step's rows and of the aggregate
                 const int Lo = p->step_L[ci][si], La = si > 0 ? p->step_L[ci][si - 1] : Lo, Lg = p->agg_L[ci][si];
                 if (s.src_chain < 0) {
-                    const uint32_t *hrow = hist + (uint64_t)v0 * B * k;
+                    const uint32_t *hrow = hist_for(s.leaf_label) + (uint64_t)v0 * B * k;
                     if (s.a == 1) {
                         Ln.begin(K_SELECT);
                         launch_combine_select(st, Lo, true, v0, nv, B, k, Ch, Chs, k, p->d_rm[s.h], col, hrow, out);
@@ -991,6 +1005,15 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 }
                 cur = out;
                 cur_stride = Chs;
+            }
+            if (C.label >= 0 && g->labels) {
+                // labelled template: the chain's vertex may sit only on vertices with its label
+                int64_t Chs_last;
+                uint64_t *rows = step_out(C.steps.size() - 1, &Chs_last);
+                const int64_t words = (int64_t)B * Chs_last * L;
+                Ln.begin(K_SELECT);
+                launch_mask_rows(st, nv, words, g->labels + v0, C.label, rows);
+                Ln.end(1, (double)nv * (1 + words * 8.0));
             }
             if (C.is_root) {
                 Ln.begin(K_REDUCE);
@@ -1205,11 +1228,15 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
 }
 
 // special cases with no DP: k = 1 (every vertex, isolated ones included), or no edges
+// label: the single vertex's label of a labelled k = 1 template, else -1
 static cc_status trivial_counts(Graph *g, const CountJob &job, int k, int64_t aut, uint64_t *counts, int32_t cap,
-                                uint64_t *maps, uint64_t *sample_out, cc_result *res)
+                                uint64_t *maps, uint64_t *sample_out, cc_result *res, int label = -1)
 {
     if (cap < 1) return fail(CC_ERR_CAPACITY, "limbs_capacity < 1");
-    const uint64_t v = (k == 1) ? (uint64_t)g->n : 0;
+    if (label >= 0 && g->h_labels.empty())
+        return fail(CC_ERR_INVALID_ARG, "labelled template on a graph without vertex labels");
+    uint64_t v = (k == 1) ? (uint64_t)g->n : 0;
+    if (k == 1 && label >= 0) v = (uint64_t)std::count(g->h_labels.begin(), g->h_labels.end(), (uint8_t)label);
     double kk = std::pow((double)k, (double)k), kf = 1;
     for (int i = 2; i <= k; i++) kf *= i;
     for (int j = 0; j < job.n_iter; j++) {
@@ -1221,7 +1248,7 @@ static cc_status trivial_counts(Graph *g, const CountJob &job, int k, int64_t au
             for (int l = 0; l < cap; l++) {
                 int64_t ov = job.sample_vertices[s];
                 sample_out[((size_t)j * job.sample_vertices.size() + s) * cap + l] =
-                    (l == 0 && k == 1 && ov >= 0 && ov < g->n) ? 1 : 0;
+                    (l == 0 && k == 1 && ov >= 0 && ov < g->n && (label < 0 || g->h_labels[ov] == label)) ? 1 : 0;
             }
     }
     if (res) {
@@ -1252,7 +1279,8 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     Template *t = tit->second.get();
     const int width = job.width_bits >= 0 ? job.width_bits : c->opt.width_bits;
     if (t->k == 1 || g->n_act == 0 || job.n_iter == 0)
-        return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res);
+        return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res,
+                              t->labels.empty() ? -1 : t->labels[0]);
     cudaStream_t st = c->stream;
     const int bcap = std::max(1, std::min({c->opt.batch > 0 ? c->opt.batch : 16, job.n_iter, 64}));
     const auto key = std::make_tuple(gid, tid, bcap, width);
@@ -1370,7 +1398,7 @@ cc_status count_multi_sync(Ctx *c, int64_t gid, const std::vector<int64_t> &tids
     if (ts[0]->k == 1 || g->n_act == 0 || job.n_iter == 0) {
         for (size_t r = 0; r < nt; r++)
             CC_TRY(trivial_counts(g, job, ts[r]->k, ts[r]->aut, counts + r * per, cap, maps ? maps + r * per : nullptr,
-                                  nullptr, res ? res + r : nullptr));
+                                  nullptr, res ? res + r : nullptr, ts[r]->labels.empty() ? -1 : ts[r]->labels[0]));
         return CC_OK;
     }
     cudaStream_t st = c->stream;

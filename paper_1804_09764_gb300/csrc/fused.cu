@@ -76,14 +76,13 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
 // step j the rows its lanes wrote in step j - 1 (__syncwarp).
 template <int Ld, int Lf = Ld>
 __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t *orow, int64_t Chs,
-                                           const LeafChain &chain, const uint32_t *__restrict__ hist, int B, int k,
-                                           int lane)
+                                           const LeafChain &chain, int B, int k, int lane)
 {
     const uint64_t *prev = orow;
     int64_t prev_s = Chs;
-    const uint32_t *hr = hist + v * (int64_t)B * k;
     for (int j = 0; j < chain.n; j++) {
         __syncwarp();
+        const uint32_t *hr = chain.hist[j] + v * (int64_t)B * k;
         const int64_t cj = chain.Ch[j], csj = chain.Chs[j];
         const int hj = chain.h[j];
         const uint32_t *pt = chain.pairs[j];
@@ -124,8 +123,7 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
                            const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
                            int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
                            const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col, uint64_t *out,
-                           int64_t out_vs, LeafChain chain, const uint32_t *__restrict__ hist,
-                           unsigned long long *next)
+                           int64_t out_vs, LeafChain chain, unsigned long long *next)
 {
     const int lane = threadIdx.x & 31;
     const int64_t R = (int64_t)B * Cps;
@@ -163,7 +161,7 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
                 }
             }
         }
-        leaf_steps<Ld, Lf>(v, v0, orow, Chs, chain, hist, B, k, lane);
+        leaf_steps<Ld, Lf>(v, v0, orow, Chs, chain, B, k, lane);
     }
 }
 
@@ -173,7 +171,7 @@ template <int Ld>
 __global__ void __launch_bounds__(kWarps * 32)
 leaf_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr, int B, int k,
                   const uint64_t *out0, int64_t out_vs, int64_t Chs, LeafChain chain,
-                  const uint32_t *__restrict__ hist, unsigned long long *next)
+                  unsigned long long *next)
 {
     const int lane = threadIdx.x & 31;
     while (true) {
@@ -182,7 +180,7 @@ leaf_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restri
         const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
         if (v >= v1) return;
         if (row_ptr[v + 1] - row_ptr[v] > split) continue;  // heavy: the p = 1 kernels
-        leaf_steps<Ld>(v, v0, out0 + (v - v0) * out_vs, Chs, chain, hist, B, k, lane);
+        leaf_steps<Ld>(v, v0, out0 + (v - v0) * out_vs, Chs, chain, B, k, lane);
     }
 }
 
@@ -229,14 +227,14 @@ template <int Ls, int Lf, int Ld>
 void gather_select_chain_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                            const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
                            int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col,
-                           uint64_t *out, int64_t out_vs, const LeafChain &chain, const uint32_t *hist,
+                           uint64_t *out, int64_t out_vs, const LeafChain &chain,
                            unsigned long long *next)
 {
     constexpr int VPT = Lf <= 2 ? 4 : 2;
     auto kfn = nb == 4 ? gather_select_chain_kernel<Ls, Lf, Ld, VPT, 4> : gather_select_chain_kernel<Ls, Lf, Ld, VPT, 2>;
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
-                                   out_vs, chain, hist, next);
+                                   out_vs, chain, next);
 }
 
 }  // namespace
@@ -245,12 +243,12 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t
                                 const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
-                                const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb)
+                                const LeafChain &chain, unsigned long long *next, int nb)
 {
     if (v1 <= v0) return;
     // Lf is Ld or Ld - 1 (the fused step's own width, at most one limb narrower)
     if (Lf < Ld - 1 || Lf > Ld || Lf < 1) Lf = Ld;
-#define CC_GC(a, f, b) if (Ls == a && Lf == f && Ld == b) return gather_select_chain_t<a, f, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, hist, next)
+#define CC_GC(a, f, b) if (Ls == a && Lf == f && Ld == b) return gather_select_chain_t<a, f, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, next)
 #define CC_GC_LS(a) CC_GC(a, 1, 1); CC_GC(a, 1, 2); CC_GC(a, 2, 2); CC_GC(a, 2, 3); CC_GC(a, 3, 3); CC_GC(a, 3, 4); CC_GC(a, 4, 4)
     CC_GC_LS(1); CC_GC_LS(2); CC_GC_LS(3); CC_GC_LS(4);
 #undef CC_GC_LS
@@ -259,13 +257,13 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t
 
 void launch_leaf_chain(cudaStream_t st, int Ld, int64_t v0, int64_t v1, int64_t split, const int64_t *row_ptr, int B,
                        int k, const uint64_t *out0, int64_t out_vs, int64_t Chs, const LeafChain &chain,
-                       const uint32_t *hist, unsigned long long *next)
+                       unsigned long long *next)
 {
     if (v1 <= v0 || chain.n <= 0) return;
     CC_DISPATCH_L(Ld, {
         auto kfn = leaf_chain_kernel<LL>;
         const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
-        kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, row_ptr, B, k, out0, out_vs, Chs, chain, hist, next);
+        kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, row_ptr, B, k, out0, out_vs, Chs, chain, next);
     });
 }
 

@@ -155,6 +155,8 @@ cc_status graph_free(Ctx *c, Graph *g)
     c->arena.free(g->row_ptr);
     c->arena.free(g->col_idx);
     c->arena.free(g->orig);
+    c->arena.free(g->labels);
+    g->labels = nullptr;
     for (auto &kv : g->splits) {
         c->arena.free(kv.second.heavy_v);
         c->arena.free(kv.second.heavy_tptr);

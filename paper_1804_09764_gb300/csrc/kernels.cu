@@ -39,7 +39,7 @@ __global__ void colour_kernel(int64_t n_act, int B, int k, const int64_t *__rest
 // warp per vertex; per-warp shared counters [B][k]
 __global__ void hist_kernel(int64_t v0, int64_t v1, int B, int k, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col_idx, const uint8_t *__restrict__ col,
-                            uint32_t *__restrict__ hist)
+                            const uint8_t *__restrict__ labels, int want, uint32_t *__restrict__ hist)
 {
     extern __shared__ uint32_t cnt_all[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -52,6 +52,7 @@ __global__ void hist_kernel(int64_t v0, int64_t v1, int B, int k, const int64_t 
         const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int64_t u = col_idx[e];
+            if (labels && labels[u] != want) continue;  // a labelled leaf counts its label only
             const uint8_t *cu = col + u * B;
             for (int b = 0; b < B; b++) atomicAdd(&cnt[b * k + cu[b]], 1u);
         }
@@ -812,6 +813,15 @@ __global__ void max_sum_kernel(int64_t n, const double *__restrict__ x, double *
     }
 }
 
+// labelled templates: rows of vertices whose label is not `want` become zero
+__global__ void mask_rows_kernel(int64_t nv, int64_t row_words, const uint8_t *__restrict__ labels, int want,
+                                 uint64_t *__restrict__ rows)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv * row_words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (labels[i / row_words] != want) rows[i] = 0;
+}
+
 __global__ void remap_kernel(int64_t nnz, int64_t n, const int32_t *__restrict__ src,
                              const int32_t *__restrict__ new_id, int32_t *__restrict__ dst)
 {
@@ -877,11 +887,18 @@ void launch_colour(cudaStream_t st, int64_t n_act, int B, int k, const int64_t *
 }
 
 void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const int64_t *row_ptr,
-                 const int32_t *col_idx, const uint8_t *col, uint32_t *hist)
+                 const int32_t *col_idx, const uint8_t *col, uint32_t *hist, const uint8_t *labels, int want)
 {
     if (v1 <= v0) return;
     size_t sh = (size_t)kWarps * B * k * sizeof(uint32_t);
-    hist_kernel<<<grid_for(v1 - v0, kWarps), kWarps * 32, sh, st>>>(v0, v1, B, k, row_ptr, col_idx, col, hist);
+    hist_kernel<<<grid_for(v1 - v0, kWarps), kWarps * 32, sh, st>>>(v0, v1, B, k, row_ptr, col_idx, col, labels, want,
+                                                                  hist);
+}
+
+void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint8_t *labels, int want, uint64_t *rows)
+{
+    if (nv <= 0 || row_words <= 0) return;
+    mask_rows_kernel<<<grid_stride_ctas(nv * row_words, 256), 256, 0, st>>>(nv, row_words, labels, want, rows);
 }
 
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,

@@ -24,8 +24,13 @@ struct ColourParams {
 void launch_colour(cudaStream_t st, int64_t n_act, int B, int k, const int64_t *orig_id,
                    const ColourParams *prm, uint8_t *col);
 
+// labels (optional): count only neighbours u with labels[u] == want
 void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const int64_t *row_ptr,
-                 const int32_t *col_idx, const uint8_t *col, uint32_t *hist);
+                 const int32_t *col_idx, const uint8_t *col, uint32_t *hist, const uint8_t *labels = nullptr,
+                 int want = 0);
+
+// labelled templates: rows[v][0 .. row_words) = 0 for v in [0, nv) with labels[v] != want
+void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint8_t *labels, int want, uint64_t *rows);
 
 // agg[v - v0] = sum_{u in N(v)} X[u]  over rows of R values; light vertices only
 // (deg <= split), heavy ones go through tasks + reduce.
@@ -125,13 +130,14 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
 // out_{j-1}[S \ {c}] * hist[c].  The rows of vertex v for step j start at
 // out[j] + (v - v0) * vs[j] (vs in 64-bit words, >= B * Chs[j] * Ld): steps that
 // share a buffer give every vertex the same slot, so no warp writes into rows
-// another warp has yet to read.  col and hist are the whole-graph arrays
+// another warp has yet to read.  col and hist[j] are whole-graph arrays
 // (indexed by global vertex id).
 struct LeafChain {
     int n;                       // number of p = 1 steps after the fused step (<= 15)
     int h[15];
     int64_t Ch[15], Chs[15], vs[15];
     const uint32_t *pairs[15];   // (h, h-1) split tables
+    const uint32_t *hist[15];    // colour histograms of the leaf's label (or of all neighbours)
     uint64_t *out[15];
 };
 // Lf: limbs of the fused step's sums and rows (Ld or Ld - 1); Ld: the leaf steps'
@@ -139,13 +145,13 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t
                                 const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
-                                const LeafChain &chain, const uint32_t *hist, unsigned long long *next, int nb = 4);
+                                const LeafChain &chain, unsigned long long *next, int nb = 4);
 
 // The chain's p = 1 steps for the light vertices of [v0, v1) whose first-step
 // rows are at out0 + (v - v0) * out_vs (written by launch_gather_select).
 void launch_leaf_chain(cudaStream_t st, int Ld, int64_t v0, int64_t v1, int64_t split, const int64_t *row_ptr, int B,
                        int k, const uint64_t *out0, int64_t out_vs, int64_t Chs, const LeafChain &chain,
-                       const uint32_t *hist, unsigned long long *next);
+                       unsigned long long *next);
 
 // a = 1 combine for heavy vertices [h0, h1) of the heavy list (aggregates from the task path)
 void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t v0, const int32_t *heavy_v, int B,

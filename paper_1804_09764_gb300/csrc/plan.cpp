@@ -87,6 +87,7 @@ namespace {
 
 struct Rooted {
     int k;
+    const uint8_t *label = nullptr;  // vertex labels (part of the canonical forms) or none
     std::vector<std::vector<int>> adj, children;
     std::vector<int> parent, size;
     std::vector<std::string> canon;
@@ -112,6 +113,7 @@ void root_at(Rooted &R, int root)
         for (int y : R.children[x]) cs.push_back(R.canon[y]);
         std::sort(cs.begin(), cs.end());
         std::string s = "(";
+        if (R.label) s += std::to_string((int)R.label[x]) + ":";
         for (auto &c : cs) s += c;
         R.canon[x] = s + ")";
         R.post.push_back(x);
@@ -138,9 +140,9 @@ int64_t step_cost(int k, int h, int a) { return binom(k, h) * binom(h, a); }
 
 }  // namespace
 
-int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj)
+int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels)
 {
-    if (k <= 2) return k == 2 ? 2 : 1;
+    if (k <= 2) return k == 2 ? (labels && labels[0] != labels[1] ? 1 : 2) : 1;
     // centre(s): strip leaves
     std::vector<int> deg(k);
     for (int i = 0; i < k; i++) deg[i] = (int)adj[i].size();
@@ -163,6 +165,7 @@ int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj)
         if (!removed[i]) centres.push_back(i);
     Rooted R;
     R.k = k;
+    R.label = labels;
     R.adj = adj;
     if (centres.size() == 1) {
         root_at(R, centres[0]);
@@ -179,6 +182,7 @@ int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj)
     std::string s1 = R.canon[c1];
     Rooted R2;
     R2.k = k;
+    R2.label = labels;
     R2.adj = cut;
     root_at(R2, c2);
     int64_t a2 = rooted_aut(R2, c2);
@@ -186,7 +190,7 @@ int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj)
 }
 
 int build_template_plan(int k, const int32_t *edges, int root, int order_mode, double avg_degree,
-                        TemplatePlan *out, std::string *err)
+                        TemplatePlan *out, std::string *err, const uint8_t *labels)
 {
     if (k < 1 || k > kMaxK) {
         *err = "k must be in 1..16";
@@ -198,6 +202,7 @@ int build_template_plan(int k, const int32_t *edges, int root, int order_mode, d
     }
     Rooted R;
     R.k = k;
+    R.label = labels;
     R.adj.assign(k, {});
     std::vector<std::pair<int, int>> E;
     for (int e = 0; e < k - 1; e++) {
@@ -300,6 +305,7 @@ int build_template_plan(int k, const int32_t *edges, int root, int order_mode, d
             C.size = R.size[x];
             C.is_root = (x == r);
             C.canon = R.canon[x];
+            C.label = labels ? labels[x] : -1;
             int a = 1;
             C.max_cols = (int)binom(k, 1);
             int prev_src = -2;
@@ -311,6 +317,7 @@ int build_template_plan(int k, const int32_t *edges, int root, int order_mode, d
                 s.p = R.size[y];
                 s.h = a + s.p;
                 s.reuse_agg = (s.src_chain == prev_src);
+                if (s.src_chain < 0 && labels) s.leaf_label = labels[y];
                 prev_src = s.src_chain;
                 C.max_cols = std::max<int>(C.max_cols, (int)binom(k, s.h));
                 C.steps.push_back(s);
@@ -358,7 +365,7 @@ int build_template_plan(int k, const int32_t *edges, int root, int order_mode, d
             if (c < bc) bc = c, best = P;
         }
     }
-    best.aut = tree_automorphisms(k, R.adj);
+    best.aut = tree_automorphisms(k, R.adj, labels);
     *out = best;
     return 0;
 }

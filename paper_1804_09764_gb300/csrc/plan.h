@@ -27,6 +27,7 @@ struct Step {
     int src_chain = -1;    // chain index holding the child's table; -1: leaf (colour histogram)
     int h = 0, a = 0, p = 0;  // |T_i|, |T_i'|, |T_i''|
     bool reuse_agg = false;   // same source as the previous step: aggregate already on hand
+    int leaf_label = -1;      // leaf child: its vertex label (-1: unlabelled template)
 };
 
 struct ChainPlan {
@@ -38,6 +39,7 @@ struct ChainPlan {
     int last_consumer = -1;  // last chain index that gathers this table
     int limbs = 1;           // 64-bit limbs of this chain's values
     int max_cols = 1;        // widest intermediate row (colour-set columns)
+    int label = -1;          // vertex label of the chain's template vertex (-1: unlabelled)
 };
 
 struct TemplatePlan {
@@ -52,12 +54,14 @@ struct TemplatePlan {
 // Validates and plans.  root = -1 lets the planner choose (cost model with the
 // given average degree).  order_mode: 0 = children largest subtree first
 // (Table 4's convention), 1 = planner's order (least combine work).
+// labels: optional vertex labels (canonical forms and |Aut| then respect them).
 // Returns 0, or a negative cc_status with *err set.
 int build_template_plan(int k, const int32_t *edges, int root, int order_mode, double avg_degree,
-                        TemplatePlan *out, std::string *err);
+                        TemplatePlan *out, std::string *err, const uint8_t *labels = nullptr);
 
-// |Aut(T)| from AHU canonical forms at the centre of the tree.
-int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj);
+// |Aut(T)| from AHU canonical forms at the centre of the tree (label-preserving
+// automorphisms when labels are given).
+int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels = nullptr);
 
 // Colex ranking of k-colour sets (combinatorial number system):
 // rank(S) = sum_i C(c_i, i+1) over the members c_0 < c_1 < ... of S.

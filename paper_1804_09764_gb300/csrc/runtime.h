@@ -65,6 +65,10 @@ struct Graph {
     // host copies used for planning
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_new_id;  // original id -> compact id or -1 (isolated)
+    // vertex labels for labelled templates, or none: host copy in the original
+    // numbering [n], device copy in the compact numbering [n_act]
+    std::vector<uint8_t> h_labels;
+    uint8_t *labels = nullptr;
     // homomorphism bounds cache, keyed by a chain's rooted canonical form and
     // the forms of the children it attaches in step order: log2 of max_v and
     // sum_v of the final bound, and per step log2 max_v of the bound after the
@@ -91,7 +95,8 @@ struct Graph {
 struct Template {
     int k = 0, root_req = -1;
     std::vector<int32_t> edges;
-    int64_t aut = 1;
+    std::vector<uint8_t> labels;  // vertex labels, or empty (unlabelled)
+    int64_t aut = 1;              // label-preserving automorphisms when labelled
 };
 
 // A template planned against a graph with a batch size and width policy.
@@ -138,6 +143,9 @@ struct PlanInstance {
     // plan (one, or several sharing their colourings) reads slot tmpl_slot[r],
     // keeps its low tmpl_L[r] limbs (exact: its total is below 2^(64 tmpl_L[r]))
     // and divides by tmpl_aut[r].
+    // colour histograms: one per distinct label of leaf children (-1: all
+    // neighbours, unlabelled templates), n_act x B x k counts each
+    std::vector<int> hist_labels;
     int n_slots = 1;
     std::vector<int> chain_slot;     // per chain: totals slot, -1 for non-root chains
     std::vector<int> tmpl_slot, tmpl_L, tmpl_root;

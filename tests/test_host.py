@@ -161,3 +161,19 @@ def test_all_trees_counts_match_the_number_of_free_trees():
         for e in trees:
             assert len(e) == k - 1
             assert O.automorphisms(k, e) >= 1  # a tree on 0..k-1 (the oracle checks connectivity)
+
+
+def test_labelled_automorphisms_library_vs_oracle(lib):
+    # AHU canonical forms with labels (library) against backtracking over
+    # label-preserving bijections (oracle)
+    import random
+
+    rng = random.Random(5)
+    for i in range(40):
+        k = rng.randrange(2, 11)
+        e = gg.prufer_tree(k, 700 + i)
+        lab = [rng.randrange(3) for _ in range(k)]
+        assert cc.cc_template_automorphisms_labelled(k, e, lab) == O.automorphisms(k, e, lab)
+    for name in ["caterpillar10", "tree12", "spider15"]:
+        k, e = gg.template_edges(name)
+        assert cc.cc_template_automorphisms_labelled(k, e, [0] * k) == cc.cc_template_automorphisms(k, e)
