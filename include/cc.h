@@ -9,6 +9,13 @@
  * k^k / k! into an estimate of the number of non-induced copies of T in G
  * (Section 2, "Subgraph-counting problem").
  *
+ * Beyond one count (cc_count, cc_count_ex): several templates over the same
+ * colourings with shared sub-tables (cc_count_multi), Algorithm 1 end to end
+ * for a (1 +- epsilon, delta) estimate (cc_iterations_for, cc_estimate),
+ * vertex-labelled templates (cc_template_load_labelled, cc_graph_set_labels),
+ * a continuous-batching serving loop (cc_submit .. cc_serve_stats_get), and
+ * the table gather on its own (cc_table_gather, cc_table_gather_noalloc).
+ *
  * Conventions shared by every entry point:
  *   - Every call returns a cc_status: CC_OK (0), CC_PENDING (1, serving only)
  *     or a negative error.  On error, cc_last_error() returns a message for the
