@@ -476,6 +476,8 @@ def main():
             dev_s += r["device_seconds"]
             launches += r["kernel_launches"]
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         wall = time.perf_counter() - t_start
     ks = ctx.kernel_stats()
     info = ctx.plan_info(gid, tid)  # the plan the timed counts used
@@ -497,10 +499,12 @@ def main():
             gid2 = ctx.graph_load_csr(rp, ci, g.n)
             if glab is not None:
                 ctx.graph_set_labels(gid2, glab)
-            r = ctx.count(gid2, tid, seed=777, n_iter=n_iter, first_iter=i * n_iter)
+            r = ctx.count(gid2, tid, seed=777, n_iter=n_iter, first_iter=replica_first_iter(rank, world, i, n_iter))
             ctx.graph_free(gid2)
             ctx2_t.append(time.perf_counter() - t)
         et = sum(ctx2_t[1:])
+        if world > 1:
+            et = max_over_ranks(et, device=f"cuda:{local}")
         e2e = {"value": info["updates_per_colouring"] * n_iter * args.steps * world / et, "unit": "updates/s",
                "h2d_bytes_per_step": int(rp.numel() * 8 + ci.numel() * 4 + (0 if glab is None else glab.size)),
                "d2h_bytes_per_step": int(n_iter * 4 * 8)}
