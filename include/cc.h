@@ -74,7 +74,7 @@ typedef struct cc_options {
                                   allocates hbm_budget_bytes itself */
     uint64_t hbm_budget_bytes; /* size of arena; with arena == NULL, 0 means 90% of the
                                   device memory free at cc_create */
-    int32_t split_threshold;   /* neighbour-list task size s (Algorithm 4); 0: default 1024 */
+    int32_t split_threshold;   /* neighbour-list task size s (Algorithm 4); 0: default 4096 */
     int32_t batch;             /* colourings processed together in one pass; 0: largest
                                   that fits the budget, at most 16 */
     int32_t block_vertices;    /* vertices per streamed block; 0: largest that fits */

@@ -491,7 +491,11 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     p->exact = width_bits == 0;
     p->Lmax = *std::max_element(p->chain_L.begin(), p->chain_L.end());
     // split threshold and batch / block size under the budget
-    p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : 1024;
+    // default s = 4096: measured on R-MAT s22 / tree-12 (ms per step) 1024: 5590,
+    // 2048: 5484, 4096: 5349, 8192: 5368, 16384: 5422, 65536: 6409 -- fewer
+    // vertices on the task path save partial rows and per-vertex combines until
+    // single warps on very long lists start to trail the launch
+    p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : 4096;
     CC_TRY(ensure_split(c, g, p->split, st));
     const Graph::Split &sp = g->splits[p->split];
     int Bmax = c->opt.batch > 0 ? c->opt.batch : 16;
