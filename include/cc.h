@@ -158,7 +158,8 @@ cc_status cc_template_load_labelled(cc_ctx *ctx, int32_t k, const int32_t *edges
  * Vertex labels of a loaded graph: labels[v] for v in [0, n) in the numbering
  * of cc_graph_load_csr (host array, copied; NULL removes the labels).  Used
  * by labelled templates only; unlabelled templates ignore them.  Drops the
- * graph's cached plans.  Errors: CC_ERR_NOT_FOUND, CC_ERR_BUDGET.
+ * graph's cached plans.  Errors: CC_ERR_NOT_FOUND, CC_ERR_BUDGET,
+ * CC_ERR_INVALID_ARG while a queued or running serving request uses the graph.
  */
 cc_status cc_graph_set_labels(cc_ctx *ctx, cc_graph_id g, const uint8_t *labels);
 

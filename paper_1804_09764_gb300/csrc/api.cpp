@@ -221,7 +221,9 @@ cc_status cc_graph_set_labels(cc_ctx *ctx, cc_graph_id g, const uint8_t *labels)
     auto it = c->graphs.find(g);
     if (it == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
     Graph *G = it->second.get();
+    if (G->in_use) return fail(CC_ERR_INVALID_ARG, "graph is used by a queued or running request");
     cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
     evict_plans(c, g);  // cached plans and captured passes hold the label pointer
     c->arena.free(G->labels);
     G->labels = nullptr;
