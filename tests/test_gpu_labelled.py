@@ -88,3 +88,19 @@ def test_labelled_and_unlabelled_templates_in_one_merged_count():
     for tid, m in zip(tids, multi):
         assert m["counts"] == c.count(gid, tid, seed=8, n_iter=2)["counts"]
     c.close()
+
+
+def test_labelled_requests_through_the_serving_loop():
+    g = gg.rmat_graph(10, seed=85)
+    glab = np.random.default_rng(4).integers(0, 3, g.n)
+    c = make_ctx(max_slots=2)
+    gid = c.graph_load(g)
+    c.graph_set_labels(gid, glab)
+    reqs = []
+    for i, name in enumerate(["P5", "caterpillar10", "tree12"]):
+        k, e = gg.template_edges(name)
+        tid = c.template_load(k, e, labels=np.random.default_rng(10 + i).integers(0, 3, k))
+        reqs.append((tid, c.submit(gid, tid, 20 + i, 3)))
+    for i, (tid, rid) in enumerate(reqs):
+        assert c.wait(rid, 3, timeout_s=120)["counts"] == c.count(gid, tid, seed=20 + i, n_iter=3)["counts"]
+    c.close()
