@@ -82,7 +82,12 @@ typedef struct cc_options {
     int32_t fused;             /* 1 (default): steps that attach a subtree to a single root
                                   vertex (a = 1) run the gather and the combine as one kernel
                                   whose neighbour sums go straight into the output row */
-    int32_t autotune;          /* 1: time candidate launch shapes on first use of a plan */
+    int32_t autotune;          /* 1: autotuner.  On the first count of a (graph, template)
+                                  with split_threshold 0, one pass is timed with each of
+                                  the split thresholds 1024, 4096 and 16384 and the fastest
+                                  kept; on the first pass of every plan, each gather site
+                                  times its kernel variants (gather_mode values, rows in
+                                  flight) and keeps the fastest. */
     int32_t max_slots;         /* serving: requests in flight at once (default 4) */
     int32_t timing;            /* 1: record per-kernel CUDA-event times (cc_kernel_stats) */
     int32_t gather_mode;       /* table-gather kernel: 1 (default): warp per row, persistent
@@ -232,6 +237,7 @@ typedef struct cc_plan_info {
                                             La-limb by an Lb-limb value into L limbs, the limb
                                             pairs i + j < L (low halves) and i + j + 1 < L (high
                                             halves) */
+    int64_t split_threshold;         /* neighbour-list task size s in use (Algorithm 4) */
 } cc_plan_info;
 
 /* Describes the plan the last cc_count of (g, t) used while it is still

@@ -91,7 +91,8 @@ class cc_plan_info(ctypes.Structure):
                 ("updates_per_colouring", ctypes.c_double), ("gather_bytes_per_colouring", ctypes.c_double),
                 ("algorithmic_bytes_per_colouring", ctypes.c_double), ("pairs_per_colouring", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_uint64), ("table4_memory", ctypes.c_int64),
-                ("table4_computation", ctypes.c_int64), ("limb_products_per_colouring", ctypes.c_double)]
+                ("table4_computation", ctypes.c_int64), ("limb_products_per_colouring", ctypes.c_double),
+                ("split_threshold", ctypes.c_int64)]
 
 
 class cc_kernel_stats(ctypes.Structure):

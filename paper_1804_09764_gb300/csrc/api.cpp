@@ -375,6 +375,7 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->table4_memory = p->tp.table4_memory;
     out->table4_computation = p->tp.table4_computation;
     out->limb_products_per_colouring = p->limb_products;
+    out->split_threshold = p->split;
     if (own) free_plan(c, own.get());
     return CC_OK;
 }

@@ -495,7 +495,12 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     // 2048: 5484, 4096: 5349, 8192: 5368, 16384: 5422, 65536: 6409 -- fewer
     // vertices on the task path save partial rows and per-vertex combines until
     // single warps on very long lists start to trail the launch
-    p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : 4096;
+    int64_t split_default = 4096;
+    if (p->tmpl_id >= 0) {
+        auto ts = c->tuned_split.find({p->graph_id, p->tmpl_id});
+        if (ts != c->tuned_split.end()) split_default = ts->second;
+    }
+    p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : split_default;
     CC_TRY(ensure_split(c, g, p->split, st));
     const Graph::Split &sp = g->splits[p->split];
     int Bmax = c->opt.batch > 0 ? c->opt.batch : 16;
@@ -1269,6 +1274,56 @@ static cc_status trivial_counts(Graph *g, const CountJob &job, int k, int64_t au
     return CC_OK;
 }
 
+// Autotuner for the neighbour-list split threshold (Algorithm 4's task size s):
+// plans the count with each candidate, times one pass of each on the count's
+// own first colourings (gather variants at their defaults, results discarded)
+// and keeps the fastest for (graph, template).  A candidate whose plan or
+// workspace does not fit is skipped.
+static cc_status tune_split(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, int width, cudaStream_t st)
+{
+    static const int64_t cands[] = {1024, 4096, 16384};
+    const int32_t saved = c->opt.split_threshold;
+    double best_ms = 1e300;
+    int64_t best = 4096;
+    for (int64_t s : cands) {
+        c->opt.split_threshold = (int32_t)s;
+        std::unique_ptr<PlanInstance> p;
+        cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &p);
+        c->opt.split_threshold = saved;
+        if (rc != CC_OK) continue;
+        p->tuned = true;  // no per-site variant trials: time the split alone
+        char *ws = (char *)arena_alloc(c, p->ws_bytes);
+        ColourParams *hp = nullptr;
+        uint64_t *ht = nullptr;
+        bool ok = ws && cudaMallocHost(&hp, sizeof(ColourParams)) == cudaSuccess &&
+                  cudaMallocHost(&ht, (size_t)8 * p->B * p->L_root * p->n_slots) == cudaSuccess;
+        float ms = 0;
+        if (ok) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaMemsetAsync(ws + p->off_err, 0, 256, st);
+            cudaEventRecord(a, st);
+            rc = run_passes(c, p.get(), ws, job, 0, 1, st, hp, ht, nullptr, nullptr, 0, nullptr, nullptr);
+            cudaEventRecord(b, st);
+            cudaStreamSynchronize(st);
+            cudaEventElapsedTime(&ms, a, b);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            ok = rc == CC_OK;
+        }
+        cudaStreamSynchronize(st);
+        if (hp) cudaFreeHost(hp);
+        if (ht) cudaFreeHost(ht);
+        c->arena.free(ws);
+        free_plan(c, p.get());
+        if (ok && ms < best_ms) best_ms = ms, best = s;
+    }
+    cudaGetLastError();
+    c->tuned_split[{gid, tid}] = best;
+    return CC_OK;
+}
+
 cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
                      uint64_t *maps, uint64_t *sample_out, cc_result *res)
 {
@@ -1286,6 +1341,9 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
         return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res,
                               t->labels.empty() ? -1 : t->labels[0]);
     cudaStream_t st = c->stream;
+    // (autotune is fixed per context, so no plan of (gid, tid) is cached yet)
+    if (c->opt.autotune && c->opt.split_threshold <= 0 && !c->tuned_split.count({gid, tid}))
+        CC_TRY(tune_split(c, gid, tid, job, width, st));
     const int bcap = std::max(1, std::min({c->opt.batch > 0 ? c->opt.batch : 16, job.n_iter, 64}));
     const auto key = std::make_tuple(gid, tid, bcap, width);
     CachedPlan *cp = nullptr;

@@ -201,6 +201,8 @@ struct Ctx {
     uint64_t use_clock = 0;
     // autotuned gather variants per (graph, template, batch), shared by later plans
     std::map<std::tuple<int64_t, int64_t, int>, std::map<std::pair<int, int>, int>> tuned_modes;
+    // autotuned neighbour-list split threshold per (graph, template)
+    std::map<std::pair<int64_t, int64_t>, int64_t> tuned_split;
     // serving
     std::unique_ptr<struct Server> server;
     Ctx();

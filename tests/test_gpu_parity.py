@@ -295,6 +295,21 @@ def test_autotuned_plan_matches_oracle():
     c.close()
 
 
+def test_autotuned_split_threshold_matches_oracle():
+    # with split_threshold 0 the first count times one pass for each candidate
+    # task size and keeps the fastest; the counts stay exact and later plans use it
+    g = gg.rmat_graph(12, seed=34)
+    assert np.diff(g.row_ptr).max() > 1024
+    k, e = gg.template_edges("tree12")
+    c = make_ctx(autotune=1, batch=2)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 1)
+    res = c.count(gid, tid, seed=7, n_iter=2, want_maps=True)
+    assert res["maps"] == oracle_maps(g, k, e, 1, 7, range(2))
+    assert c.plan_info(gid, tid)["split_threshold"] in (1024, 4096, 16384)
+    c.close()
+
+
 @pytest.mark.parametrize("fused", [0, 1])
 def test_fused_and_unfused_gather_select(fused):
     # a = 1 steps: fused gather + select kernel against the separate kernels, with
