@@ -177,3 +177,21 @@ def test_labelled_automorphisms_library_vs_oracle(lib):
     for name in ["caterpillar10", "tree12", "spider15"]:
         k, e = gg.template_edges(name)
         assert cc.cc_template_automorphisms_labelled(k, e, [0] * k) == cc.cc_template_automorphisms(k, e)
+
+
+def test_header_is_plain_c_and_cpp(tmp_path):
+    # include/cc.h is the C ABI: it must compile as strict C11 and as C++
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    src = tmp_path / "t.c"
+    src.write_text('#include "cc.h"\nint main(void) { cc_options o; cc_default_options(&o); '
+                   'return (int)sizeof(cc_plan_info) > 0 ? 0 : 1; }\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                           "-I", inc, str(src)])
+    if shutil.which("g++"):
+        subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++", "-I", inc,
+                               str(src)])
