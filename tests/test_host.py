@@ -195,3 +195,19 @@ def test_header_is_plain_c_and_cpp(tmp_path):
     if shutil.which("g++"):
         subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++", "-I", inc,
                                str(src)])
+
+
+def test_c_caller_compiles_and_links_against_the_library(lib, tmp_path):
+    # the boundary is a C ABI: a plain C program builds against include/cc.h
+    # and the shared library (running it needs a GPU)
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    build_dir = os.path.dirname(cc.LIB_PATH)
+    exe = tmp_path / "c_abi_example"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi_example.c"), "-L", build_dir, "-lcc_gb300",
+                           f"-Wl,-rpath,{build_dir}", "-o", str(exe)])
+    assert exe.exists()
