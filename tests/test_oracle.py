@@ -343,3 +343,45 @@ def test_labelled_automorphisms_against_permutations():
             lab = [rng.randrange(2) for _ in range(k)]
             assert O.automorphisms(k, e, lab) == brute_aut_labelled(k, e, lab)
         assert O.automorphisms(k, e, [0] * k) == O.automorphisms(k, e)
+
+
+# ----------------------------------------------------------------- the table gather on its own
+
+def _ints(X):
+    return [[sum(int(X[u, c, i]) << (64 * i) for i in range(X.shape[2])) for c in range(X.shape[1])]
+            for u in range(X.shape[0])]
+
+
+def test_neighbour_sum_closed_forms_on_a_star():
+    # hub 0 and leaves 1..N: the hub sums the leaves' rows, every leaf gets the hub's row
+    N, L = 6, 2
+    g = gg.star_graph(N)
+    X = np.random.default_rng(1).integers(0, 2 ** 63, size=(N + 1, 3, L), dtype=np.uint64)
+    out = _ints(O.neighbour_sum(g, X, L))
+    x = _ints(X)
+    M = 1 << (64 * L)
+    assert out[0] == [sum(x[u][c] for u in range(1, N + 1)) % M for c in range(3)]
+    for leaf in range(1, N + 1):
+        assert out[leaf] == x[0]
+
+
+def test_neighbour_sum_wraps_modulo_its_width():
+    g = gg.star_graph(2)
+    for L in (1, 2, 3):
+        X = np.full((3, 1, L), np.uint64(2 ** 64 - 1))
+        assert _ints(O.neighbour_sum(g, X, L))[0][0] == (1 << (64 * L)) - 2
+
+
+def test_neighbour_sum_of_colour_indicators_gives_edge_map_counts():
+    # gathering the one-hot colour table gives each vertex its neighbours'
+    # colour histogram; the colours other than its own count the colourful
+    # maps of an edge rooted at it (the C dynamic program, per vertex)
+    g = gg.rmat_graph(8, seed=12)
+    k = 2  # the edge template's colours
+    colours = O.colour(9, 0, range(g.n), k)
+    X = np.zeros((g.n, k, 1), dtype=np.uint64)
+    X[np.arange(g.n), colours.astype(np.int64), 0] = 1
+    hist = O.neighbour_sum(g, X, 1)[:, :, 0]
+    assert (hist.sum(axis=1) == np.diff(g.row_ptr)).all()
+    _, pv = O.count_maps(g, 2, [(0, 1)], 0, colours=colours, per_vertex=True)
+    assert pv == [int(hist[v].sum() - hist[v, colours[v]]) for v in range(g.n)]
