@@ -385,3 +385,18 @@ def test_neighbour_sum_of_colour_indicators_gives_edge_map_counts():
     assert (hist.sum(axis=1) == np.diff(g.row_ptr)).all()
     _, pv = O.count_maps(g, 2, [(0, 1)], 0, colours=colours, per_vertex=True)
     assert pv == [int(hist[v].sum() - hist[v, colours[v]]) for v in range(g.n)]
+
+
+def test_run_reports_brute_force_copies_per_colouring():
+    # Algorithm 1 over colourings: per colouring, copies = colourful maps / |Aut|
+    k, edges = SMALL_TEMPLATES["star4"]
+    g = gg.random_graph_gnp(8, 0.6, seed=41)
+    out = O.run(g, k, edges, seed=3, n_iter=4, root=0, first_iter=2)
+    aut = brute_aut(k, edges)
+    assert out["aut"] == aut
+    for j in range(4):
+        colours = O.colour(3, 2 + j, range(g.n), k)
+        assert out["copies"][j] == brute_maps(g, colours, k, edges) // aut
+    assert out["mean"] == pytest.approx(sum(c * k ** k / math.factorial(k) for c in out["copies"]) / 4, rel=1e-12)
+    with pytest.raises(ArithmeticError):
+        O.copies_from_maps(7, 2)
