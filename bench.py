@@ -92,11 +92,17 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def instance_file_name(name: str) -> str:
+    """File-name form of a kernel instantiation: gather_select_chain_kernel<2,2,3>
+    -> gather_select_chain_kernel_2_2_3."""
+    return name.replace("<", "_").replace(",", "_").replace(">", "")
+
+
 def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
-    summary (profiles/traffic_<kernel>_<workload>.json), or None when absent or
-    taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.json")
+    """DRAM bytes per launch of the kernel instantiation `kernel` on `workload`
+    from a committed ncu summary (profiles/traffic_<kernel>_<workload>.json), or
+    None when absent or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{instance_file_name(kernel)}_{workload}.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -515,26 +521,38 @@ def main():
         return
     peak, peak_kind = measured_peaks()
     kinds = {k_: v for k_, v in ks.items() if isinstance(v, dict) and v["launches"] > 0}
-    dom = max(kinds.items(), key=lambda kv: kv[1]["seconds"])
-    dname, d = dom
-    achieved = d["bytes"] / d["seconds"] / 1e9 if d["seconds"] > 0 else 0.0
+    insts = ctx.kernel_instances()
+    # the dominant kernel: the instantiation with the most timed device time
+    timed = [(kind, nm, st) for kind, d in insts.items() for nm, st in d.items() if st["seconds"] > 0]
+    dkind, dname, d = max(timed, key=lambda x: x[2]["seconds"])
+    kernel_s = sum(v["seconds"] for v in kinds.values())
+    achieved = d["bytes"] / d["seconds"] / 1e9
+    avg_s = d["seconds"] / d["timed_launches"]
+    traffic = profiled_traffic(dname, args.workload)
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": profiled_traffic(dname, args.workload),
-                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                "launches": d["launches"], "avg_launch_ms": 1e3 * d["seconds"] / d["launches"],
-                "share_of_kernel_time": d["seconds"] / sum(v["seconds"] for v in kinds.values())}
-    if dname == "combine" and info["limb_products_per_colouring"] > 0:
+                "traffic": traffic,
+                "dram_achieved": traffic / avg_s / 1e9 if traffic else None,
+                "dram_frac": traffic / avg_s / 1e9 / peak if traffic else None,
+                "algorithmic_bytes_per_launch": d["bytes"] / d["timed_launches"],
+                "launches": d["timed_launches"], "avg_launch_ms": 1e3 * avg_s,
+                "share_of_kernel_time": d["seconds"] / kernel_s}
+    if dkind == "combine" and info["limb_products_per_colouring"] > 0:
+        d = kinds["combine"]
         # the general combine is bound by its wide multiply-adds: 64-bit limb
         # products per second against the rate the GPU sustains on registers
         lp = info["limb_products_per_colouring"] * n_iter * args.steps
         alu_peak = ctx.limb_product_rate()
         a_alu = lp / d["seconds"] / 1e12
-        roofline.update({"bound": "alu", "achieved": a_alu, "peak": alu_peak / 1e12,
+        roofline.update({"bound": "alu", "kernel": "combine (all instantiations)", "achieved": a_alu,
+                         "peak": alu_peak / 1e12,
                          "unit": "T limb-products/s", "frac": a_alu / (alu_peak / 1e12),
                          "peak_kind": "measured (cc_limb_product_rate: register-resident 64-bit multiply-adds)",
-                         "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
-                         "limb_products_per_launch": lp / d["launches"]})
+                         "hbm_achieved_gbs": d["bytes"] / d["seconds"] / 1e9, "hbm_peak_gbs": peak,
+                         "limb_products_per_launch": lp / d["launches"], "launches": d["launches"],
+                         "avg_launch_ms": 1e3 * d["seconds"] / d["launches"],
+                         "share_of_kernel_time": d["seconds"] / kernel_s, "traffic": None,
+                         "dram_achieved": None, "dram_frac": None})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         s, dt, desc, gs, k2, e2, root2 = oracle_sample(wl, target_s=15.0)
@@ -565,7 +583,10 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "kernels": {k_: {"launches": v["launches"], "ms": round(1e3 * v["seconds"], 3),
-                         "GBps": (v["bytes"] / v["seconds"] / 1e9) if v["seconds"] else None}
+                         "GBps": (v["bytes"] / v["seconds"] / 1e9) if v["seconds"] else None,
+                         "instances": {nm: {"launches": st["launches"], "ms": round(1e3 * st["seconds"], 3),
+                                            "GBps": (st["bytes"] / st["seconds"] / 1e9) if st["seconds"] else None}
+                                       for nm, st in insts[k_].items()}}
                     for k_, v in kinds.items()},
     }
     print(json.dumps(line), flush=True)

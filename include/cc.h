@@ -83,9 +83,12 @@ typedef struct cc_options {
                                   vertex (a = 1) run the gather and the combine as one kernel
                                   whose neighbour sums go straight into the output row */
     int32_t autotune;          /* 1: autotuner.  On the first count of a (graph, template)
-                                  with split_threshold 0, one pass is timed with each of
-                                  the split thresholds 1024, 4096 and 16384 and the fastest
-                                  kept; on the first pass of every plan, each gather site
+                                  it times the plan's shape, by coordinate descent over the
+                                  options left at 0: split_threshold (1024, 4096, 16384),
+                                  col_chunks (default rule, 1, 4, 16) and block_vertices
+                                  (largest block that fits, 1/2, 1/4); each candidate runs
+                                  one untimed pass, then the median of three timed passes
+                                  decides.  On the first pass of every plan, each gather site
                                   times its kernel variants (gather_mode values, rows in
                                   flight) and keeps the fastest. */
     int32_t max_slots;         /* serving: requests in flight at once (default 4) */
@@ -238,11 +241,54 @@ typedef struct cc_plan_info {
                                             pairs i + j < L (low halves) and i + j + 1 < L (high
                                             halves) */
     int64_t split_threshold;         /* neighbour-list task size s in use (Algorithm 4) */
+    int64_t block_vertices;          /* vertices per streamed block in use */
+    int32_t col_chunks;              /* column segments in use (cc_options.col_chunks meaning) */
+    int32_t shape_tuned;             /* 1: split, segments and block size come from the autotuner */
 } cc_plan_info;
 
 /* Describes the plan the last cc_count of (g, t) used while it is still
  * cached, else plans a count of opt.batch (default 16) colourings. */
 cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan_info *out);
+
+/*
+ * The steps of a plan: one row per application of Eq. 1 (Section 2.1), i.e.
+ * per child attached to a chain (chains in post-order, the root chain last),
+ * with the integer widths the homomorphism bounds gave it and how the last
+ * pass ran it for the light vertices (those with at most split_threshold
+ * neighbours) of the first vertex block.  Describes the cached plan of the
+ * last count of (g, t) under the context's width policy; with no such plan
+ * (or a plan that has not run) every path is CC_PATH_NOT_RUN.
+ *   out[cap] receives min(cap, steps) rows; *n_steps the number of steps.
+ * Errors: CC_ERR_INVALID_ARG (NULL ctx or n_steps, cap < 0), CC_ERR_NOT_FOUND.
+ */
+#define CC_PATH_NOT_RUN        0
+#define CC_PATH_CHAIN_KERNEL   1  /* gather + a = 1 combine, and in the same kernel the chain's p = 1 steps */
+#define CC_PATH_IN_CHAIN       2  /* a p = 1 step run inside the chain kernel of its chain's first step */
+#define CC_PATH_SEGMENTED      3  /* column-segmented gather + a = 1 combine, then the leaf-chain kernel */
+#define CC_PATH_FUSED_SELECT   4  /* gather + a = 1 combine in one kernel */
+#define CC_PATH_GATHER_SELECT  5  /* table gather kernel, then the a = 1 combine */
+#define CC_PATH_GATHER_COMBINE 6  /* table gather kernel, then the general combine */
+#define CC_PATH_LEAF_SELECT    7  /* a = 1 step attaching a leaf: select from the colour histogram */
+#define CC_PATH_LEAF_COMBINE   8  /* p = 1 step: combine with the colour histogram */
+typedef struct cc_step_info {
+    int32_t chain, step;     /* chain index, step within the chain */
+    int32_t vertex;          /* template vertex the chain is rooted at */
+    int32_t child;           /* template vertex whose subtree this step attaches */
+    int32_t h, a, p;         /* |T_i|, |T_i'|, |T_i''| */
+    int32_t src_chain;       /* chain whose table is gathered; -1 for a leaf child */
+    int32_t is_root;         /* 1 for the root chain */
+    int32_t limbs;           /* 64-bit limbs the step's own bound needs */
+    int32_t agg_limbs;       /* limbs of its neighbour sums */
+    int32_t src_limbs;       /* limbs of the gathered table (0 for a leaf child) */
+    int32_t chain_limbs;     /* limbs of the chain's table (root chain: of the totals) */
+    int32_t path;            /* CC_PATH_* */
+    int32_t kernel_limbs[3]; /* limb template arguments of that path's kernel:
+                                chain kernel <Ls, Lf, Ld>; fused select <Ls, -, Ld>;
+                                gather + combine <Ls, Lagg, Lout>; leaf paths <Lin, -, Lout> */
+} cc_step_info;
+
+cc_status cc_plan_steps_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_step_info *out, int32_t cap,
+                            int32_t *n_steps);
 
 /* Per-kernel CUDA-event statistics (opt.timing = 1); cumulative since reset.
  * Kinds, in order: colour; hist (colour histograms of N(v), the leaf gather);
@@ -263,6 +309,27 @@ typedef struct cc_kernel_stats {
 
 cc_status cc_kernel_stats_get(cc_ctx *ctx, cc_kernel_stats *out);
 cc_status cc_kernel_stats_reset(cc_ctx *ctx);
+
+/* Statistics per kernel instantiation since the last reset: one row per
+ * (kind, instantiation) launched, sorted by kind then name.  The name carries
+ * the limb template arguments, e.g. "gather_select_chain_kernel<2,2,3>".
+ * Launches are always counted; seconds, bytes and timed_launches (opt.timing
+ * = 1) cover the timed groups of launches in which this instantiation was the
+ * only kernel, so seconds / timed_launches is its average launch duration and
+ * bytes / seconds its algorithmic rate.
+ *   out[cap] receives min(cap, rows) rows; *n (optional) the number of rows.
+ * Errors: CC_ERR_INVALID_ARG (NULL ctx, cap < 0, out NULL with cap > 0). */
+typedef struct cc_instance_stats {
+    char name[96];           /* NUL-terminated, truncated if longer */
+    int32_t kind;            /* index into cc_kernel_stats */
+    int32_t reserved;
+    int64_t launches;
+    int64_t timed_launches;
+    double seconds;
+    double bytes;
+} cc_instance_stats;
+
+cc_status cc_kernel_instance_stats_get(cc_ctx *ctx, cc_instance_stats *out, int32_t cap, int32_t *n);
 
 /*
  * Eq. 1's neighbour sum for one count table on its own (the table-gather step):
@@ -298,14 +365,15 @@ cc_status cc_table_gather(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const 
  *   split tasks; larger inputs return CC_ERR_CAPACITY before any gather kernel
  *   runs (raise split_threshold to need fewer tasks).
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture.
- *   The call synchronises `stream` once (to read the task count) and returns
- *   with the gather kernels queued on `stream`.  All calls share the array and
+ *   (cudaGetSymbolAddress) and caches it.
+ *   Every call synchronises `stream` once, to read the task count back, and
+ *   returns with the gather kernels queued on `stream`; because of that
+ *   synchronisation and read-back no call can be captured into a CUDA graph.  All calls share the array and
  *   each call rewrites what it reads, so nothing needs clearing between calls,
  *   but calls whose kernels overlap on the GPU race on the array: serialise them.
  *   Calls no cudaMalloc, cudaFree or other allocating routine.
- * Errors: CC_ERR_INVALID_ARG, CC_ERR_CAPACITY, CC_ERR_CUDA.
+ * Errors: CC_ERR_INVALID_ARG (also for a decreasing row_ptr, found on the
+ * device before any gather kernel runs), CC_ERR_CAPACITY, CC_ERR_CUDA.
  */
 cc_status cc_table_gather_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                                   const uint64_t *X, uint64_t *agg, int64_t values, int32_t limbs,

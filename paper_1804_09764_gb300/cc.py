@@ -92,7 +92,24 @@ class cc_plan_info(ctypes.Structure):
                 ("algorithmic_bytes_per_colouring", ctypes.c_double), ("pairs_per_colouring", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_uint64), ("table4_memory", ctypes.c_int64),
                 ("table4_computation", ctypes.c_int64), ("limb_products_per_colouring", ctypes.c_double),
-                ("split_threshold", ctypes.c_int64)]
+                ("split_threshold", ctypes.c_int64), ("block_vertices", ctypes.c_int64),
+                ("col_chunks", ctypes.c_int32), ("shape_tuned", ctypes.c_int32)]
+
+
+class cc_step_info(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("chain", "step", "vertex", "child", "h", "a", "p", "src_chain",
+                                             "is_root", "limbs", "agg_limbs", "src_limbs", "chain_limbs",
+                                             "path")] + [("kernel_limbs", ctypes.c_int32 * 3)]
+
+
+STEP_PATHS = {0: "not_run", 1: "chain_kernel", 2: "in_chain", 3: "segmented", 4: "fused_select",
+              5: "gather_select", 6: "gather_combine", 7: "leaf_select", 8: "leaf_combine"}
+
+
+class cc_instance_stats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 96), ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class cc_kernel_stats(ctypes.Structure):
@@ -141,6 +158,8 @@ def load_library(path: str = LIB_PATH):
         "cc_plan_info_get": (I32, [P, I64, I64, P]),
         "cc_kernel_stats_get": (I32, [P, P]),
         "cc_kernel_stats_reset": (I32, [P]),
+        "cc_plan_steps_get": (I32, [P, I64, I64, P, I32, P]),
+        "cc_kernel_instance_stats_get": (I32, [P, P, I32, P]),
         "cc_submit": (I32, [P, P, P]),
         "cc_poll": (I32, [P, I64, P, P, I32]),
         "cc_wait": (I32, [P, I64, I64, P, P, I32]),
@@ -428,6 +447,33 @@ class Context:
         info = cc_plan_info()
         _check(self._lib.cc_plan_info_get(self._h, gid, tid, ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in cc_plan_info._fields_}
+
+    def plan_steps(self, gid: int, tid: int) -> list:
+        """cc_plan_steps_get: one dict per DP step (widths and the path the last pass took)."""
+        n = ctypes.c_int32()
+        _check(self._lib.cc_plan_steps_get(self._h, gid, tid, None, 0, ctypes.byref(n)))
+        arr = (cc_step_info * max(1, n.value))()
+        _check(self._lib.cc_plan_steps_get(self._h, gid, tid, arr, n.value, ctypes.byref(n)))
+        out = []
+        for r in arr[:n.value]:
+            d = {f: getattr(r, f) for f, _ in cc_step_info._fields_ if f != "kernel_limbs"}
+            d["kernel_limbs"] = tuple(r.kernel_limbs)
+            d["path"] = STEP_PATHS.get(d["path"], str(d["path"]))
+            out.append(d)
+        return out
+
+    def kernel_instances(self) -> dict:
+        """cc_kernel_instance_stats_get: {kind name: {instantiation: stats}}."""
+        names = [n for n in self.kernel_stats() if n != "total_launches"]
+        n = ctypes.c_int32()
+        _check(self._lib.cc_kernel_instance_stats_get(self._h, None, 0, ctypes.byref(n)))
+        arr = (cc_instance_stats * max(1, n.value))()
+        _check(self._lib.cc_kernel_instance_stats_get(self._h, arr, n.value, ctypes.byref(n)))
+        out = {nm: {} for nm in names}
+        for r in arr[:n.value]:
+            out[names[r.kind]][r.name.decode()] = dict(launches=r.launches, timed_launches=r.timed_launches,
+                                                       seconds=r.seconds, bytes=r.bytes)
+        return out
 
     def kernel_stats(self) -> dict:
         s = cc_kernel_stats()

@@ -376,7 +376,95 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->table4_computation = p->tp.table4_computation;
     out->limb_products_per_colouring = p->limb_products;
     out->split_threshold = p->split;
+    out->block_vertices = p->V;
+    out->col_chunks = p->col_chunks;
+    out->shape_tuned = p->shape_tuned ? 1 : 0;
     if (own) free_plan(c, own.get());
+    return CC_OK;
+}
+
+cc_status cc_plan_steps_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_step_info *out, int32_t cap,
+                            int32_t *n_steps)
+{
+    if (!ctx || !n_steps || cap < 0 || (cap > 0 && !out)) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    auto git = c->graphs.find(g);
+    auto tit = c->templates.find(t);
+    if (git == c->graphs.end() || tit == c->templates.end()) return fail(CC_ERR_NOT_FOUND, "unknown handle");
+    *n_steps = 0;
+    if (tit->second->k == 1 || git->second->n_act == 0) return CC_OK;
+    const PlanInstance *cached = nullptr;
+    uint64_t last = 0;
+    for (auto &kv : c->plan_cache)
+        if (std::get<0>(kv.first) == g && std::get<1>(kv.first) == t && std::get<3>(kv.first) == c->opt.width_bits &&
+            kv.second.last_use >= last) {
+            cached = kv.second.p.get();
+            last = kv.second.last_use;
+        }
+    std::unique_ptr<PlanInstance> own;
+    if (!cached) {
+        int n_iter = c->opt.batch > 0 ? c->opt.batch : 16;
+        CC_TRY(make_plan(c, g, t, n_iter, c->opt.width_bits, c->stream, &own));
+    }
+    const PlanInstance *p = cached ? cached : own.get();
+    int32_t n = 0;
+    for (size_t ci = 0; ci < p->tp.chains.size(); ci++) {
+        const ChainPlan &C = p->tp.chains[ci];
+        for (size_t si = 0; si < C.steps.size(); si++, n++) {
+            if (n >= cap) continue;
+            const Step &st = C.steps[si];
+            cc_step_info &r = out[n];
+            std::memset(&r, 0, sizeof r);
+            r.chain = (int32_t)ci;
+            r.step = (int32_t)si;
+            r.vertex = C.vertex;
+            r.child = st.child;
+            r.h = st.h;
+            r.a = st.a;
+            r.p = st.p;
+            r.src_chain = st.src_chain;
+            r.is_root = C.is_root ? 1 : 0;
+            r.limbs = p->step_L[ci][si];
+            r.agg_limbs = p->agg_L[ci][si];
+            r.src_limbs = st.src_chain >= 0 ? p->chain_L[st.src_chain] : 0;
+            r.chain_limbs = p->chain_L[ci];
+            if (ci < p->step_path.size() && si < p->step_path[ci].size()) {
+                const auto &sp = p->step_path[ci][si];
+                r.path = sp.path;
+                r.kernel_limbs[0] = sp.l0;
+                r.kernel_limbs[1] = sp.l1;
+                r.kernel_limbs[2] = sp.l2;
+            }
+        }
+    }
+    *n_steps = n;
+    if (own) free_plan(c, own.get());
+    return CC_OK;
+}
+
+cc_status cc_kernel_instance_stats_get(cc_ctx *ctx, cc_instance_stats *out, int32_t cap, int32_t *n)
+{
+    if (!ctx || cap < 0 || (cap > 0 && !out)) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int32_t rows = 0;
+    for (int kind = 0; kind < CC_KERNEL_KINDS; kind++)
+        for (const auto &kv : c->timer.instances[kind]) {
+            if (rows < cap) {
+                cc_instance_stats &r = out[rows];
+                std::memset(&r, 0, sizeof r);
+                std::strncpy(r.name, kv.first.c_str(), sizeof r.name - 1);
+                r.kind = kind;
+                r.launches = kv.second.launches;
+                r.timed_launches = kv.second.timed_launches;
+                r.seconds = kv.second.seconds;
+                r.bytes = kv.second.bytes;
+            }
+            rows++;
+        }
+    if (n) *n = rows;
     return CC_OK;
 }
 
@@ -406,6 +494,7 @@ cc_status cc_kernel_stats_reset(cc_ctx *ctx)
         c->timer.launches[i] = 0;
         c->timer.seconds[i] = 0;
         c->timer.bytes[i] = 0;
+        c->timer.instances[i].clear();
     }
     c->launches = 0;
     return CC_OK;

@@ -170,6 +170,7 @@ void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, 
     const size_t smem = (size_t)(Cas * La + Cps * Lb) * 8;
     const bool staged = smem >= (16u << 10) && smem <= (200u << 10);
     const int64_t rows = nv * B;
+    note_launch(staged ? "combine_generic_smem_kernel" : "combine_generic_kernel", L, La, Lb);
 #define CC_CG(l, a, b)                                                                              \
     case ((l - 1) * 16 + (a - 1) * 4 + (b - 1)):                                                    \
         if (staged) {                                                                               \

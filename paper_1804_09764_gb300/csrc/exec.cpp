@@ -168,9 +168,9 @@ static int vertex_group(int nch) { return nch > 1 ? 4 : 1; }
 // -> row chain of dependent loads, and a chain's leaf steps then need a kernel
 // of their own (R-MAT s22 / tree-12, two steps: whole rows 8.2 s; every light
 // vertex segmented 9.5 s; only those of degree >= 64 segmented 8.55 s).
-static int64_t fused_split(const Ctx *c, int64_t v0, int64_t v1, int64_t R, int Ls, int *nch)
+static int64_t fused_split(int col_chunks, int64_t v0, int64_t v1, int64_t R, int Ls, int *nch)
 {
-    *nch = c->opt.col_chunks > 0 ? column_segments(R, Ls, c->opt.col_chunks) : 1;
+    *nch = col_chunks > 0 ? column_segments(R, Ls, col_chunks) : 1;
     return *nch > 1 ? v1 : v0;
 }
 
@@ -496,9 +496,16 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     // vertices on the task path save partial rows and per-vertex combines until
     // single warps on very long lists start to trail the launch
     int64_t split_default = 4096;
+    int block_div = 1;
+    p->col_chunks = c->opt.col_chunks;
     if (p->tmpl_id >= 0) {
-        auto ts = c->tuned_split.find({p->graph_id, p->tmpl_id});
-        if (ts != c->tuned_split.end()) split_default = ts->second;
+        auto ts = c->tuned_shape.find({p->graph_id, p->tmpl_id});
+        if (ts != c->tuned_shape.end()) {
+            split_default = ts->second.split;
+            if (c->opt.col_chunks == 0) p->col_chunks = ts->second.col_chunks;
+            if (c->opt.block_vertices == 0) block_div = std::max(1, ts->second.block_div);
+            p->shape_tuned = true;
+        }
     }
     p->split = c->opt.split_threshold > 0 ? c->opt.split_threshold : split_default;
     CC_TRY(ensure_split(c, g, p->split, st));
@@ -515,6 +522,11 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
             Lo = layout_for(*p, *g, sp, B, V);
             if (Lo.bytes + (64ull << 20) <= room) {
                 found = true;
+                if (block_div > 1 && V > 4096) {
+                    // autotuned: a fraction of the largest block that fits (fits too)
+                    V = std::max<int64_t>(4096, (V + block_div - 1) / block_div);
+                    Lo = layout_for(*p, *g, sp, B, V);
+                }
                 p->B = B;
                 p->V = V;
                 break;
@@ -657,6 +669,7 @@ struct Launcher {
     void begin(int k_)
     {
         kind = k_;
+        take_launch_names();  // names noted outside a timed kind are dropped
         if (T.on) {
             ea = get_event();
             cudaEventRecord(ea, st);
@@ -665,13 +678,26 @@ struct Launcher {
     void end(int nlaunch, double bytes)
     {
         c->launches += nlaunch;
+        // the instantiations this bracket launched; one alone gets its time
+        std::string only;
+        int64_t n_only = 0;
+        for (auto &nm : take_launch_names()) {
+            T.instances[kind][nm].launches++;
+            if (n_only == 0 || nm == only) {
+                only = nm;
+                n_only++;
+            } else {
+                n_only = -1 << 30;
+            }
+        }
+        if (n_only <= 0) only.clear();
         T.launches[kind] += nlaunch;
         T.total_launches += nlaunch;
         T.bytes[kind] += bytes;
         if (T.on) {
             cudaEvent_t eb = get_event();
             cudaEventRecord(eb, st);
-            T.pending.push_back({ea, eb, kind, bytes});
+            T.pending.push_back({ea, eb, kind, bytes, only, n_only});
         }
     }
 };
@@ -684,7 +710,15 @@ static void drain_timer(Ctx *c)
     auto &T = c->timer;
     for (auto &q : T.pending) {
         float ms = 0;
-        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) T.seconds[q.kind] += ms * 1e-3;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            T.seconds[q.kind] += ms * 1e-3;
+            if (!q.only.empty()) {
+                auto &in = T.instances[q.kind][q.only];
+                in.seconds += ms * 1e-3;
+                in.bytes += q.bytes;
+                in.timed_launches += q.n;
+            }
+        }
         T.pool.push_back(q.a);
         T.pool.push_back(q.b);
     }
@@ -725,10 +759,18 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         lab >= 0 ? g->labels : nullptr, lab);
         Ln.end(1, (double)g->nnz * (4 + B) + (double)g->n_act * (8 + 4.0 * B * k));
     }
+    if (p->step_path.size() != tp.chains.size()) {
+        p->step_path.assign(tp.chains.size(), {});
+        for (size_t ci = 0; ci < tp.chains.size(); ci++) p->step_path[ci].assign(tp.chains[ci].steps.size(), {});
+    }
     for (size_t ci = 0; ci < tp.chains.size(); ci++) {
         const ChainPlan &C = tp.chains[ci];
         const int L = p->chain_L[ci];
         for (size_t bi = 0; bi < p->blocks.size(); bi++) {
+            // the path of step si for the light vertices of the first block
+            auto note_path = [&](size_t si, int path, int l0, int l1, int l2) {
+                if (bi == 0) p->step_path[ci][si] = {path, l0, l1, l2};
+            };
             const int64_t v0 = p->blocks[bi].first, v1 = p->blocks[bi].second, nv = v1 - v0;
             const auto &hv = p->heavy[bi];
             const uint64_t *cur = nullptr;
@@ -803,8 +845,12 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 // [v0, vmid): column-segmented gather + select into the slots, then the
                 // leaf kernel; [vmid, v1): the one-kernel chain (whole rows)
                 int nch = 1;
-                const int64_t vmid = fused_split(c, v0, v1, R, Ls, &nch);
+                const int64_t vmid = fused_split(p->col_chunks, v0, v1, R, Ls, &nch);
                 int nl = 0;
+                // the fused step at its own width (at most one limb below the chain's)
+                const int Lf = std::max(L - 1, std::min(L, p->step_L[ci][0]));
+                note_path(0, vmid > v0 ? CC_PATH_SEGMENTED : CC_PATH_CHAIN_KERNEL, Ls, vmid > v0 ? L : Lf, L);
+                for (size_t j = 1; j <= nleaf; j++) note_path(j, CC_PATH_IN_CHAIN, Ls, vmid > v0 ? L : Lf, L);
                 Ln.begin(K_FUSED);
                 if (vmid > v0) {
                     launch_gather_select(st, Ls, L, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
@@ -818,8 +864,6 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     // rows of vertex v stay at (v - v0) * stride: shift the outputs by vmid - v0
                     LeafChain lt = lc;
                     for (int j = 0; j < lt.n; j++) lt.out[j] += (vmid - v0) * lt.vs[j];
-                    // the fused step at its own width (at most one limb below the chain's)
-                    const int Lf = std::max(L - 1, std::min(L, p->step_L[ci][0]));
                     launch_gather_select_chain(st, Ls, Lf, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
                                                Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col,
                                                out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt,
@@ -832,7 +876,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     Ln.begin(K_HEAVY);
                     uint64_t *part = (uint64_t *)W(p->off_partial);
                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                        next_counter(), 4, column_segments(R, Ls, c->opt.col_chunks));
+                                        next_counter(), 4, column_segments(R, Ls, p->col_chunks));
                     launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                     launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch0, Chs0, Cps, p->d_rm[s.h], col,
                                         agg, out0);
@@ -857,10 +901,12 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 if (s.src_chain < 0) {
                     const uint32_t *hrow = hist_for(s.leaf_label) + (uint64_t)v0 * B * k;
                     if (s.a == 1) {
+                        note_path(si, CC_PATH_LEAF_SELECT, 0, 0, Lo);
                         Ln.begin(K_SELECT);
                         launch_combine_select(st, Lo, true, v0, nv, B, k, Ch, Chs, k, p->d_rm[s.h], col, hrow, out);
                         Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + 4.0 * k + 1));
                     } else {
+                        note_path(si, CC_PATH_LEAF_COMBINE, La, 0, Lo);
                         Ln.begin(K_CHIST);
                         launch_combine_hist(st, Lo, La, nv, B, k, Ch, Chs, cur_stride, s.h, p->d_pairs.at({s.h, s.a}),
                                             cur, hrow, out);
@@ -880,10 +926,11 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     };
                     const double e_blk = (double)(g->h_row_ptr[v1] - g->h_row_ptr[v0]);
                     const double light_bytes = sel_bytes(e_blk - (double)hv.edges, (double)(nv - (hv.h1 - hv.h0)));
+                    note_path(si, CC_PATH_FUSED_SELECT, Ls, 0, Lo);
                     Ln.begin(K_FUSED);
                     const auto site = std::make_pair((int)ci, (int)si);
                     int nch = 1;
-                    const int64_t vmid = fused_split(c, v0, v1, R, Ls, &nch);
+                    const int64_t vmid = fused_split(p->col_chunks, v0, v1, R, Ls, &nch);
                     // [v0, vmid) column-segmented, [vmid, v1) whole rows
                     auto fused_run = [&](int nb) {
                         if (vmid > v0)
@@ -919,7 +966,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         Ln.begin(K_HEAVY);
                         uint64_t *part = (uint64_t *)W(p->off_partial);
                         launch_gather_tasks(st, Ls, Lo, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                            next_counter(), nb_tasks, column_segments(R, Ls, c->opt.col_chunks));
+                                            next_counter(), nb_tasks, column_segments(R, Ls, p->col_chunks));
                         launch_gather_reduce(st, Lo, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                         launch_select_heavy(st, Lo, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
                                             agg, out);
@@ -958,8 +1005,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                             else
                                 launch_gather_light(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
                                                     gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
-                                                    column_segments(R, Ls, c->opt.col_chunks),
-                                                    vertex_group(column_segments(R, Ls, c->opt.col_chunks)));
+                                                    column_segments(R, Ls, p->col_chunks),
+                                                    vertex_group(column_segments(R, Ls, p->col_chunks)));
                             Ln.end(1, light_bytes);
                             if (hv.t1 > hv.t0) {
                                 Ln.begin(K_HEAVY);
@@ -975,7 +1022,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 else
                                     launch_gather_tasks(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
                                                         gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
-                                                        column_segments(R, Ls, c->opt.col_chunks));
+                                                        column_segments(R, Ls, p->col_chunks));
                                 launch_gather_reduce(st, Lg, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
                                 Ln.end(2, heavy_bytes);
@@ -1001,11 +1048,13 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         }
                     }
                     if (s.a == 1) {
+                        note_path(si, CC_PATH_GATHER_SELECT, Ls, Lg, Lo);
                         Ln.begin(K_SELECT);
                         // a = 1: the output is the aggregate (Lg == Lo)
                         launch_combine_select(st, Lo, false, v0, nv, B, k, Ch, Chs, Cps, p->d_rm[s.h], col, agg, out);
                         Ln.end(1, (double)nv * B * ((Ch + Cp) * 8.0 * Lo + 1));
                     } else {
+                        note_path(si, CC_PATH_GATHER_COMBINE, Ls, Lg, Lo);
                         Ln.begin(K_COMBINE);
                         launch_combine_generic(st, Lo, La, Lg, nv, B, Ch, Chs, cur_stride, Cps, binom(s.h, s.a),
                                                p->d_pairs.at({s.h, s.a}), cur, agg, out);
@@ -1274,53 +1323,118 @@ static cc_status trivial_counts(Graph *g, const CountJob &job, int k, int64_t au
     return CC_OK;
 }
 
-// Autotuner for the neighbour-list split threshold (Algorithm 4's task size s):
-// plans the count with each candidate, times one pass of each on the count's
-// own first colourings (gather variants at their defaults, results discarded)
-// and keeps the fastest for (graph, template).  A candidate whose plan or
-// workspace does not fit is skipped.
-static cc_status tune_split(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, int width, cudaStream_t st)
+// Autotuner for the plan's shape: the neighbour-list split threshold
+// (Algorithm 4's task size s), the column segments of the gathers and the
+// vertex-block size.  A candidate shape is planned, run for one untimed pass
+// and then timed over three passes of the count's own first colourings (gather
+// variants at their defaults, results discarded); its time is the median.  A
+// candidate whose plan or workspace does not fit, or whose pass reports a
+// kernel wait that ran out, is skipped; a CUDA error ends the tuning with that
+// error.  Coordinate descent: the split threshold first (1024, 4096, 16384),
+// then the column segments (the default rule, whole rows, 4 and 16 segments)
+// at the best threshold, then the block size (the largest that fits, a half,
+// a quarter); options the caller set are not tuned.
+static cc_status time_shape(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, int width, cudaStream_t st,
+                            const Ctx::TunedShape &shape, double *ms_out)
 {
-    static const int64_t cands[] = {1024, 4096, 16384};
-    const int32_t saved = c->opt.split_threshold;
-    double best_ms = 1e300;
-    int64_t best = 4096;
-    for (int64_t s : cands) {
-        c->opt.split_threshold = (int32_t)s;
-        std::unique_ptr<PlanInstance> p;
-        cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &p);
-        c->opt.split_threshold = saved;
-        if (rc != CC_OK) continue;
-        p->tuned = true;  // no per-site variant trials: time the split alone
-        char *ws = (char *)arena_alloc(c, p->ws_bytes);
-        ColourParams *hp = nullptr;
-        uint64_t *ht = nullptr;
-        bool ok = ws && cudaMallocHost(&hp, sizeof(ColourParams)) == cudaSuccess &&
-                  cudaMallocHost(&ht, (size_t)8 * p->B * p->L_root * p->n_slots) == cudaSuccess;
-        float ms = 0;
-        if (ok) {
-            cudaEvent_t a, b;
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
+    *ms_out = -1;
+    const auto key = std::make_pair(gid, tid);
+    auto had = c->tuned_shape.find(key);
+    const bool had_shape = had != c->tuned_shape.end();
+    const Ctx::TunedShape saved = had_shape ? had->second : Ctx::TunedShape{};
+    c->tuned_shape[key] = shape;
+    std::unique_ptr<PlanInstance> p;
+    cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &p);
+    if (had_shape)
+        c->tuned_shape[key] = saved;
+    else
+        c->tuned_shape.erase(key);
+    if (rc == CC_ERR_BUDGET) return CC_OK;
+    if (rc != CC_OK) return rc;
+    p->tuned = true;  // no per-site variant trials: time the shape alone
+    char *ws = (char *)arena_alloc(c, p->ws_bytes);
+    ColourParams *hp = nullptr;
+    uint64_t *ht = nullptr;
+    std::vector<float> times;
+    if (ws && cudaMallocHost(&hp, sizeof(ColourParams)) == cudaSuccess &&
+        cudaMallocHost(&ht, (size_t)8 * p->B * p->L_root * p->n_slots) == cudaSuccess) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        for (int rep = 0; rep < 4 && rc == CC_OK; rep++) {
             cudaMemsetAsync(ws + p->off_err, 0, 256, st);
             cudaEventRecord(a, st);
             rc = run_passes(c, p.get(), ws, job, 0, 1, st, hp, ht, nullptr, nullptr, 0, nullptr, nullptr);
             cudaEventRecord(b, st);
-            cudaStreamSynchronize(st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (rc == CC_OK && e != cudaSuccess)
+                rc = fail(CC_ERR_CUDA, std::string("autotuner pass: ") + cudaGetErrorString(e));
+            int kerr = 0;
+            if (rc == CC_OK) {
+                e = cudaMemcpy(&kerr, ws + p->off_err, sizeof kerr, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) rc = fail(CC_ERR_CUDA, std::string("autotuner: ") + cudaGetErrorString(e));
+            }
+            if (rc != CC_OK || kerr) {
+                times.clear();
+                break;
+            }
+            float ms = 0;
             cudaEventElapsedTime(&ms, a, b);
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-            ok = rc == CC_OK;
+            if (rep > 0) times.push_back(ms);  // the first pass warms up
         }
-        cudaStreamSynchronize(st);
-        if (hp) cudaFreeHost(hp);
-        if (ht) cudaFreeHost(ht);
-        c->arena.free(ws);
-        free_plan(c, p.get());
-        if (ok && ms < best_ms) best_ms = ms, best = s;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
     }
-    cudaGetLastError();
-    c->tuned_split[{gid, tid}] = best;
+    cudaStreamSynchronize(st);
+    if (hp) cudaFreeHost(hp);
+    if (ht) cudaFreeHost(ht);
+    if (ws) c->arena.free(ws);
+    free_plan(c, p.get());
+    if (rc != CC_OK) return rc;
+    if (!times.empty()) {
+        std::sort(times.begin(), times.end());
+        *ms_out = times[times.size() / 2];
+    }
+    return CC_OK;
+}
+
+static cc_status tune_shape(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, int width, cudaStream_t st)
+{
+    Ctx::TunedShape best;
+    double best_ms = -1;
+    auto consider = [&](const Ctx::TunedShape &cand) -> cc_status {
+        double ms = -1;
+        CC_TRY(time_shape(c, gid, tid, job, width, st, cand, &ms));
+        if (ms >= 0 && (best_ms < 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = cand;
+        }
+        return CC_OK;
+    };
+    CC_TRY(consider(best));
+    if (c->opt.split_threshold <= 0)
+        for (int64_t s : {1024, 16384}) {
+            Ctx::TunedShape cand = best;
+            cand.split = s;
+            CC_TRY(consider(cand));
+        }
+    if (c->opt.col_chunks == 0) {
+        const Ctx::TunedShape base = best;
+        for (int ch : {1, 4, 16}) {
+            Ctx::TunedShape cand = base;
+            cand.col_chunks = ch;
+            CC_TRY(consider(cand));
+        }
+    }
+    if (c->opt.block_vertices == 0) {
+        const Ctx::TunedShape base = best;
+        for (int dv : {2, 4}) {
+            Ctx::TunedShape cand = base;
+            cand.block_div = dv;
+            CC_TRY(consider(cand));
+        }
+    }
+    c->tuned_shape[{gid, tid}] = best;
     return CC_OK;
 }
 
@@ -1342,8 +1456,9 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
                               t->labels.empty() ? -1 : t->labels[0]);
     cudaStream_t st = c->stream;
     // (autotune is fixed per context, so no plan of (gid, tid) is cached yet)
-    if (c->opt.autotune && c->opt.split_threshold <= 0 && !c->tuned_split.count({gid, tid}))
-        CC_TRY(tune_split(c, gid, tid, job, width, st));
+    if (c->opt.autotune && !c->tuned_shape.count({gid, tid}) &&
+        (c->opt.split_threshold <= 0 || c->opt.col_chunks == 0 || c->opt.block_vertices == 0))
+        CC_TRY(tune_shape(c, gid, tid, job, width, st));
     const int bcap = std::max(1, std::min({c->opt.batch > 0 ? c->opt.batch : 16, job.n_iter, 64}));
     const auto key = std::make_tuple(gid, tid, bcap, width);
     CachedPlan *cp = nullptr;

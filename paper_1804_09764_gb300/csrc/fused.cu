@@ -198,6 +198,7 @@ void gather_select_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t sp
     auto kfn = nb == 4 ? gather_select_kernel<Ls, Ld, VPT, 4> : gather_select_kernel<Ls, Ld, VPT, 2>;
     const int64_t items = (v1 - v0 + G - 1) / G * nch;
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(items, kWarps));
+    note_launch("gather_select_kernel", Ls, Ld);
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
                                    out_vs > 0 ? out_vs : (int64_t)B * Chs * Ld, next, nch, G);
 }
@@ -233,6 +234,7 @@ void gather_select_chain_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int6
     constexpr int VPT = Lf <= 2 ? 4 : 2;
     auto kfn = nb == 4 ? gather_select_chain_kernel<Ls, Lf, Ld, VPT, 4> : gather_select_chain_kernel<Ls, Lf, Ld, VPT, 2>;
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
+    note_launch("gather_select_chain_kernel", Ls, Lf, Ld);
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
                                    out_vs, chain, next);
 }
@@ -263,6 +265,7 @@ void launch_leaf_chain(cudaStream_t st, int Ld, int64_t v0, int64_t v1, int64_t 
     CC_DISPATCH_L(Ld, {
         auto kfn = leaf_chain_kernel<LL>;
         const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
+        note_launch("leaf_chain_kernel", LL);
         kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, row_ptr, B, k, out0, out_vs, Chs, chain, next);
     });
 }

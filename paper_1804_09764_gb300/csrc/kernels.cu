@@ -861,6 +861,7 @@ void gather_light_t(cudaStream_t st, bool pf, int nb, int64_t v0, int64_t v1, in
     if (!next || pf) nch = G = 1;
     const int64_t items = (v1 - v0 + G - 1) / G * nch;
     const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(items, kWarps)) : grid_for(v1 - v0, kWarps);
+    note_launch("gather_light_kernel", Ls, Ld);
     k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next, nch, G);
 }
 
@@ -874,10 +875,34 @@ void gather_tasks_t(cudaStream_t st, bool pf, int nb, int64_t t0, int64_t t1, co
     if (!next || pf) nch = 1;
     const int64_t items = (t1 - t0) * nch;
     const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(items, kWarps)) : grid_for(t1 - t0, kWarps);
+    note_launch("gather_tasks_kernel", Ls, Ld);
     k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next, nch);
 }
 
 }  // namespace
+
+namespace {
+thread_local std::vector<std::string> t_launch_names;
+}
+
+void note_launch(const char *kernel, int a, int b, int c)
+{
+    std::string s(kernel);
+    if (a >= 0) {
+        s += "<" + std::to_string(a);
+        if (b >= 0) s += "," + std::to_string(b);
+        if (c >= 0) s += "," + std::to_string(c);
+        s += ">";
+    }
+    t_launch_names.push_back(std::move(s));
+}
+
+std::vector<std::string> take_launch_names()
+{
+    std::vector<std::string> r;
+    r.swap(t_launch_names);
+    return r;
+}
 
 void launch_colour(cudaStream_t st, int64_t n_act, int B, int k, const int64_t *orig_id,
                    const ColourParams *prm, uint8_t *col)
@@ -1096,6 +1121,7 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
                           uint64_t *agg)
 {
     if (h1 <= h0) return;
+    note_launch("gather_reduce_kernel", Ld);
     CC_DISPATCH_L(Ld, gather_reduce_kernel<LL><<<grid_for(h1 - h0, kWarps), kWarps * 32, 0, st>>>(
                           h0, h1, v0, t0, heavy_v, heavy_tptr, partial, R, agg));
 }
@@ -1106,6 +1132,7 @@ void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0,
 {
     const int64_t total = nv * B * Chs;
     if (total == 0) return;
+    note_launch(agg_is_hist ? "combine_select_kernel<hist>" : "combine_select_kernel", L);
     if (agg_is_hist) {
         CC_DISPATCH_L(L, combine_select_kernel<LL, true><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
                              total, v0, B, k, Ch, Chs, Cps, rm, col, agg, out));
@@ -1124,6 +1151,7 @@ void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int 
     L = std::max(1, std::min(L, 4));
     La = std::max(1, std::min(La, L));
     const unsigned g = grid_stride_ctas(total, 256);
+    note_launch("combine_hist_kernel", L, La);
 #define CC_CH(l, a)                                                                                        \
     case ((l - 1) * 4 + (a - 1)):                                                                          \
         combine_hist_kernel<l, a><<<g, 256, 0, st>>>(total, k, Ch, Chs, Cas, h, pairs, act, hist, out); \
@@ -1142,6 +1170,7 @@ void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t
 {
     const int64_t total = (h1 - h0) * B * Chs;
     if (total <= 0) return;
+    note_launch("select_heavy_kernel", L);
     CC_DISPATCH_L(L, select_heavy_kernel<LL><<<grid_stride_ctas(total, 256), 256, 0, st>>>(
                          h0, h1, v0, heavy_v, B, k, Ch, Chs, Cps, rm, col, agg, out));
 }

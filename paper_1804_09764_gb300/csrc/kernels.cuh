@@ -11,10 +11,19 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 namespace cc {
+
+// Names of the kernel instantiations the launch wrappers below issued on the
+// calling thread, e.g. "gather_select_chain_kernel<2,2,3>" (template limb
+// arguments; -1 leaves one out).  take_launch_names() returns them and clears
+// the list; the executor files them under the kernel kind being timed.
+void note_launch(const char *kernel, int a = -1, int b = -1, int c = -1);
+std::vector<std::string> take_launch_names();
 
 struct ColourParams {
     uint64_t hj[64];  // F(F(seed) + j) for the colourings of the pass (b < B <= 64)

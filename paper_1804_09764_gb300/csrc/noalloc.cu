@@ -37,7 +37,7 @@ struct Header {
     long long tasks;     // T
     long long heavy;     // H
     long long overflow;  // 1 if the lists did not fit
-    long long pad;
+    long long bad_rows;  // 1 if some row_ptr[v + 1] < row_ptr[v]
 };
 
 struct Layout {
@@ -115,7 +115,7 @@ noalloc_tasks_kernel(long long n, const int64_t *__restrict__ row_ptr, long long
     int32_t *heavy_v = reinterpret_cast<int32_t *>(scratch + L.off_heavy_v);
     int64_t *tptr = reinterpret_cast<int64_t *>(scratch + L.off_tptr);
     long long T = 0, H = 0;
-    int overflow = 0;
+    int overflow = 0, bad = 0;
     for (long long base = 0; base < n; base += (long long)kBuildThreads * kPerThread) {
         const long long v0 = base + (long long)threadIdx.x * kPerThread;
         long long my_t = 0, my_h = 0;
@@ -123,6 +123,7 @@ noalloc_tasks_kernel(long long n, const int64_t *__restrict__ row_ptr, long long
             const long long v = v0 + i;
             if (v >= n) break;
             const long long d = row_ptr[v + 1] - row_ptr[v];
+            bad |= d < 0;
             if (d > split) {
                 my_t += (d + split - 1) / split;
                 my_h += 1;
@@ -156,12 +157,14 @@ noalloc_tasks_kernel(long long n, const int64_t *__restrict__ row_ptr, long long
         H += hsum;
         overflow = __syncthreads_or(overflow);
     }
+    bad = __syncthreads_or(bad);
     if (threadIdx.x == 0) {
         const bool fits = !overflow && T <= L.max_tasks && H <= L.max_heavy;
         if (fits) tptr[H] = T;
         hdr->tasks = T;
         hdr->heavy = H;
         hdr->overflow = fits ? 0 : 1;
+        hdr->bad_rows = bad ? 1 : 0;
     }
 }
 
@@ -217,6 +220,7 @@ extern "C" cc_status cc_table_gather_noalloc(int64_t n, const int64_t *row_ptr, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hdr, scratch, sizeof hdr, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(CC_ERR_CUDA, std::string("task list: ") + cudaGetErrorString(e));
+    if (hdr.bad_rows) return fail(CC_ERR_INVALID_ARG, "row_ptr decreases");
     if (hdr.overflow)
         return fail(CC_ERR_CAPACITY, "split lists need " + std::to_string(hdr.tasks) + " tasks of " +
                                          std::to_string(row_bytes) + " bytes; the static scratch holds " +

@@ -8,6 +8,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -119,6 +120,8 @@ struct PlanInstance {
     struct BlockHeavy { int64_t h0, h1, t0, t1, edges; };
     std::vector<BlockHeavy> heavy;
     int64_t split = 1024;
+    int col_chunks = 0;     // column segments in use (cc_options.col_chunks meaning)
+    bool shape_tuned = false;
     int64_t max_tasks = 0;
     // device constants (arena): rm tables per h, pair tables per (h, a)
     void *consts = nullptr;
@@ -150,6 +153,10 @@ struct PlanInstance {
     std::vector<int> chain_slot;     // per chain: totals slot, -1 for non-root chains
     std::vector<int> tmpl_slot, tmpl_L, tmpl_root;
     std::vector<int64_t> tmpl_aut;
+    // how the last pass ran each (chain, step) for the light vertices of the
+    // first vertex block: a CC_PATH_* code and the kernel's limb arguments
+    struct StepPath { int path = 0, l0 = 0, l1 = 0, l2 = 0; };
+    std::vector<std::vector<StepPath>> step_path;
     // several templates: chains and gathered updates per colouring had each
     // been planned alone
     int sep_chains = 0;
@@ -164,7 +171,12 @@ struct KernelTimer {
     double seconds[CC_KERNEL_KINDS] = {0};
     double bytes[CC_KERNEL_KINDS] = {0};
     int64_t total_launches = 0;
-    struct Pending { cudaEvent_t a, b; int kind; double bytes; };
+    // kernel instantiations launched under each kind (note_launch names):
+    // launches, and the time and algorithmic bytes of the timed brackets that
+    // launched that instantiation alone
+    struct Inst { int64_t launches = 0, timed_launches = 0; double seconds = 0, bytes = 0; };
+    std::map<std::string, Inst> instances[CC_KERNEL_KINDS];
+    struct Pending { cudaEvent_t a, b; int kind; double bytes; std::string only; int64_t n; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
 };
@@ -201,8 +213,11 @@ struct Ctx {
     uint64_t use_clock = 0;
     // autotuned gather variants per (graph, template, batch), shared by later plans
     std::map<std::tuple<int64_t, int64_t, int>, std::map<std::pair<int, int>, int>> tuned_modes;
-    // autotuned neighbour-list split threshold per (graph, template)
-    std::map<std::pair<int64_t, int64_t>, int64_t> tuned_split;
+    // autotuned plan shape per (graph, template): neighbour-list split
+    // threshold, column segments (0: the default rule) and the divisor of the
+    // largest vertex block that fits (1: the largest)
+    struct TunedShape { int64_t split = 4096; int col_chunks = 0; int block_div = 1; };
+    std::map<std::pair<int64_t, int64_t>, TunedShape> tuned_shape;
     // serving
     std::unique_ptr<struct Server> server;
     Ctx();

@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "CSRGraph", "csr_from_edges", "er_graph", "rmat_graph", "cycle_graph",
     "complete_graph", "star_graph", "prufer_tree", "TEMPLATES", "template_edges",
-    "random_graph_gnp",
+    "random_graph_gnp", "complete_bipartite_graph", "disjoint_union",
 ]
 
 
@@ -195,6 +195,29 @@ def star_graph(leaves: int) -> CSRGraph:
     """K_{1,leaves}: hub 0 joined to vertices 1..leaves."""
     v = np.arange(1, leaves + 1)
     return csr_from_edges(leaves + 1, np.stack([np.zeros_like(v), v], 1), f"star{leaves}")
+
+
+def complete_bipartite_graph(c: int, N: int) -> CSRGraph:
+    """K_{c,N}: vertices 0..c-1 (degree N) each joined to all of c..c+N-1 (degree c)."""
+    lo = np.repeat(np.arange(c, dtype=np.int64), N)
+    hi = np.tile(np.arange(c, c + N, dtype=np.int64), c)
+    return _csr_from_unique_pairs(c + N, lo, hi, f"K{c},{N}")
+
+
+def disjoint_union(*graphs: CSRGraph) -> CSRGraph:
+    """The graphs side by side: the vertices of graphs[i] follow those of
+    graphs[i-1], and no edge joins two of them."""
+    n = sum(g.n for g in graphs)
+    rp = [np.zeros(1, dtype=np.int64)]
+    ci = []
+    vo = eo = 0
+    for g in graphs:
+        rp.append(g.row_ptr[1:] + eo)
+        ci.append(g.col_idx.astype(np.int64) + vo)
+        vo += g.n
+        eo += g.nnz
+    col = np.concatenate(ci).astype(np.int32) if ci else np.zeros(0, dtype=np.int32)
+    return CSRGraph(n, np.concatenate(rp), col, "+".join(g.name for g in graphs))
 
 
 def prufer_tree(k: int, seed: int) -> list[tuple[int, int]]:

@@ -30,12 +30,15 @@ def test_profiled_traffic_only_for_the_sources_it_was_taken_on(tmp_path, monkeyp
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: digest)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     os.makedirs(tmp_path / "profiles")
-    rec = {"kernel": "fused", "workload": "w", "dram_bytes_per_launch": 1.5e9, "kernel_source_digest": digest}
-    with open(tmp_path / "profiles" / "traffic_fused_w.json", "w") as f:
+    name = "gather_select_chain_kernel<2,2,3>"
+    rec = {"kernel": name, "workload": "w", "dram_bytes_per_launch": 1.5e9, "kernel_source_digest": digest}
+    path = tmp_path / "profiles" / "traffic_gather_select_chain_kernel_2_2_3_w.json"
+    with open(path, "w") as f:
         json.dump(rec, f)
-    assert bench.profiled_traffic("fused", "w") == 1.5e9
-    assert bench.profiled_traffic("fused", "other") is None
+    assert bench.profiled_traffic(name, "w") == 1.5e9
+    assert bench.profiled_traffic(name, "other") is None
+    assert bench.profiled_traffic("gather_select_chain_kernel<1,2,2>", "w") is None
     # a record taken on other sources is not used
-    with open(tmp_path / "profiles" / "traffic_fused_w.json", "w") as f:
+    with open(path, "w") as f:
         json.dump(dict(rec, kernel_source_digest="0000000000000000"), f)
-    assert bench.profiled_traffic("fused", "w") is None
+    assert bench.profiled_traffic(name, "w") is None

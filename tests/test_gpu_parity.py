@@ -296,8 +296,9 @@ def test_autotuned_plan_matches_oracle():
 
 
 def test_autotuned_split_threshold_matches_oracle():
-    # with split_threshold 0 the first count times one pass for each candidate
-    # task size and keeps the fastest; the counts stay exact and later plans use it
+    # with split_threshold, col_chunks and block_vertices at 0 the first count
+    # times candidate shapes (task size, column segments, block size) and keeps
+    # the fastest; the counts stay exact and later plans use it
     g = gg.rmat_graph(12, seed=34)
     assert np.diff(g.row_ptr).max() > 1024
     k, e = gg.template_edges("tree12")
@@ -306,7 +307,11 @@ def test_autotuned_split_threshold_matches_oracle():
     tid = c.template_load(k, e, 1)
     res = c.count(gid, tid, seed=7, n_iter=2, want_maps=True)
     assert res["maps"] == oracle_maps(g, k, e, 1, 7, range(2))
-    assert c.plan_info(gid, tid)["split_threshold"] in (1024, 4096, 16384)
+    info = c.plan_info(gid, tid)
+    assert info["split_threshold"] in (1024, 4096, 16384)
+    assert info["col_chunks"] in (0, 1, 4, 16) and info["shape_tuned"] == 1
+    res = c.count(gid, tid, seed=7, n_iter=2, first_iter=2, want_maps=True)
+    assert res["maps"] == oracle_maps(g, k, e, 1, 7, range(2, 4))
     c.close()
 
 
