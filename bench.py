@@ -486,6 +486,7 @@ def main():
             torch.distributed.barrier()
         wall = time.perf_counter() - t_start
     ks = ctx.kernel_stats()
+    insts = ctx.kernel_instances()  # the timed steps only (before the end-to-end counts)
     info = ctx.plan_info(gid, tid)  # the plan the timed counts used
     elapsed = dev_s
     if world > 1:
@@ -521,7 +522,6 @@ def main():
         return
     peak, peak_kind = measured_peaks()
     kinds = {k_: v for k_, v in ks.items() if isinstance(v, dict) and v["launches"] > 0}
-    insts = ctx.kernel_instances()
     # the dominant kernel: the instantiation with the most timed device time
     timed = [(kind, nm, st) for kind, d in insts.items() for nm, st in d.items() if st["seconds"] > 0]
     dkind, dname, d = max(timed, key=lambda x: x[2]["seconds"])

@@ -829,6 +829,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     lc.Chs[j - 1] = cs;
                     lc.vs[j - 1] = vstride(j, cs);
                     lc.pairs[j - 1] = p->d_pairs.at({C.steps[j].h, C.steps[j].a});
+                    lc.rm[j - 1] = p->d_rm[C.steps[j].h];
                     lc.hist[j - 1] = hist_for(C.steps[j].leaf_label);
                 }
                 const int64_t nh = hv.h1 - hv.h0;

@@ -8,27 +8,64 @@ namespace cc {
 
 namespace {
 
+// Zeros of a fused step's output row where the vertex's colour is not in S
+// (and in the padding columns): no neighbour sum scatters to these entries.
+template <int L>
+__device__ __forceinline__ void zero_missing(uint64_t *orow, int B, int k, int Ch, int Chs,
+                                             const uint16_t *__restrict__ rm_h, const uint8_t *cv, int lane)
+{
+    RowPos pos;
+    pos.init(lane, Chs);
+    for (int i = lane; i < B * Chs; i += 32, pos.step(32, Chs))
+        if (pos.s >= Ch || rm_h[pos.s * k + cv[pos.b]] == 0xFFFFu) {
+            Wide<L> z;
+            wzero(z);
+            wstore(orow + (int64_t)i * L, z);
+        }
+}
+
+// One warp sweep of a fused step: the neighbour sums acc[q] of the values
+// base + q * 32 + lane (< b1) of colouring b, set T, go to out[b][T u {col_b}]
+// (skipped when col_b is in T).  pos tracks (b, T) of base + lane and is left
+// at base + 32 * VPT + lane.
+template <int L, int VPT>
+__device__ __forceinline__ void scatter_sums(uint64_t *orow, const Wide<L> (&acc)[VPT], int base, int b1, int Cp,
+                                             int Cps, int Chs, int k, const uint16_t *__restrict__ add_p,
+                                             const uint8_t *cv, RowPos &pos, int lane)
+{
+#pragma unroll
+    for (int q = 0; q < VPT; q++) {
+        if (base + q * 32 + lane < b1 && pos.s < Cp) {
+            const uint32_t d = add_p[pos.s * k + cv[pos.b]];
+            if (d != 0xFFFFu) wstore(orow + ((int64_t)pos.b * Chs + d) * L, acc[q]);
+        }
+        pos.step(32, Cps);
+    }
+}
+
 // Fused gather + a = 1 combine (Eq. 1 with T_i' a single vertex): the sum of
 // the neighbour rows agg[T] goes straight to out[T u {col(v)}] (skipped when
 // col(v) is in T); entries S of the output with col(v) not in S are zero.  The
-// aggregate never reaches memory.  Persistent warps pull light vertices from
-// `next`; heavy vertices are left to the task path.
+// aggregate never reaches memory.  Persistent warps pull work items from
+// `next` (the next claim is requested while the current item runs); heavy
+// vertices are left to the task path.
 template <int Ls, int Ld, int VPT, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                      const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
-                     int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
+                     int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,
                      const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col,
                      uint64_t *__restrict__ out, int64_t out_vs, unsigned long long *next, int nch, int G)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t R = (int64_t)B * Cps;
-    const int64_t ngrp = (v1 - v0 + G - 1) / G, cw = segment_width<VPT>(R, nch);
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t i = (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (i >= ngrp * nch) return;
+    const int R = B * Cps;
+    const int64_t ngrp = (v1 - v0 + G - 1) / G;
+    const int cw = (int)segment_width<VPT>(R, nch);
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(next, 1ull);
+    int64_t i = (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    while (i < ngrp * nch) {
+        if (lane == 0) got = atomicAdd(next, 1ull);  // the next item, awaited after this one
         const int64_t seg = i / ngrp, grp = i - seg * ngrp;
         const int64_t va = v0 + grp * G, vb = min(v1, va + G);
         for (int64_t v = va; v < vb; v++) {
@@ -36,77 +73,101 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
             if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select
             uint64_t *orow = out + (v - v0) * out_vs;
             const uint8_t *cv = col + v * B;
-            // zeros where the vertex's colour is not in S (and in the padding):
-            // written by segment 0 only; no segment scatters to these entries
-            if (seg == 0)
-                for (int64_t i2 = lane; i2 < (int64_t)B * Chs; i2 += 32) {
-                    const int64_t b = i2 / Chs, S = i2 - b * Chs;
-                    if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
-                        Wide<Ld> z;
-                        wzero(z);
-                        wstore(orow + i2 * Ld, z);
-                    }
-                }
-            const int64_t b1 = min(R, (seg + 1) * cw);
-            for (int64_t base = seg * cw; base < b1; base += 32 * VPT) {
+            if (seg == 0) zero_missing<Ld>(orow, B, k, Ch, Chs, rm_h, cv, lane);  // no segment scatters there
+            const int b0 = (int)seg * cw, b1 = min(R, b0 + cw);
+            RowPos pos;
+            pos.init(b0 + lane, Cps);
+            for (int base = b0; base < b1; base += 32 * VPT) {
                 Wide<Ld> acc[VPT];
 #pragma unroll
                 for (int q = 0; q < VPT; q++) wzero(acc[q]);
                 accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-                // scatter: agg column T of colouring b lands on T u {col}
-#pragma unroll
-                for (int q = 0; q < VPT; q++) {
-                    const int64_t c = base + q * 32 + lane;
-                    if (c < b1) {
-                        const int64_t b = c / Cps, T = c - b * Cps;
-                        if (T < Cp) {
-                            const uint32_t d = add_p[T * k + cv[b]];
-                            if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Ld, acc[q]);
-                        }
-                    }
-                }
+                scatter_sums<Ld, VPT>(orow, acc, base, b1, Cp, Cps, Chs, k, add_p, cv, pos, lane);
             }
         }
+        i = (int64_t)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 
 // The chain's p = 1 steps for vertex v, from its first-step row orow (stride
 // Chs per colouring, Lf-limb values; Lf <= Ld): out_j[S] = sum over c in S of
 // out_{j-1}[S \ {c}] * hist[v][c], written with Ld limbs.  The warp reads in
-// step j the rows its lanes wrote in step j - 1 (__syncwarp).
-template <int Ld, int Lf = Ld>
-__device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t *orow, int64_t Chs,
+// step j the rows its lanes wrote in step j - 1 (__syncwarp).  Only the
+// colours that some neighbour of v has (in any colouring of the pass) give
+// non-zero terms: when they are fewer than half of |S| the sum runs over them
+// (rm_h[S * k + c]: rank of S \ {c}, or c outside S), otherwise over the
+// split table of S, QB terms loaded at a time (fewer for wide values, to stay
+// within the registers of three CTAs per SM).
+template <int Ld, int Lf = Ld, int QB = (Ld >= 3 ? 2 : 4)>
+__device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t *orow, int Chs,
                                            const LeafChain &chain, int B, int k, int lane)
 {
     const uint64_t *prev = orow;
-    int64_t prev_s = Chs;
+    int prev_s = Chs;
+    const int Bk = B * k;
     for (int j = 0; j < chain.n; j++) {
+        const uint32_t *hr = chain.hist[j] + v * (int64_t)Bk;
+        // neighbour colour counts; with B * k <= 32 they stay in the lanes'
+        // registers and are read with shuffles
+        const uint32_t hv = lane < Bk ? hr[lane] : 0u;
+        unsigned nz = 0;
+        for (int t = lane; t < Bk; t += 32)
+            if ((t < 32 ? hv : hr[t]) != 0) nz |= 1u << (t % k);
+        nz = __reduce_or_sync(0xffffffffu, nz);
         __syncwarp();
-        const uint32_t *hr = chain.hist[j] + v * (int64_t)B * k;
-        const int64_t cj = chain.Ch[j], csj = chain.Chs[j];
-        const int hj = chain.h[j];
-        const uint32_t *pt = chain.pairs[j];
+        const int cj = (int)chain.Ch[j], csj = (int)chain.Chs[j], hj = chain.h[j];
+        const bool sparse = 2 * __popc(nz) < hj;
+        const uint16_t *__restrict__ rm = chain.rm[j];
+        const uint32_t *__restrict__ pt = chain.pairs[j];
         uint64_t *dst = chain.out[j] + (v - v0) * chain.vs[j];
-        for (int64_t i = lane; i < (int64_t)B * csj; i += 32) {
-            const int64_t b = i / csj, S = i - b * csj;
+        const int Lp = j == 0 ? Lf : Ld;  // limbs of the rows read
+        // count of colour c among the neighbours, colouring b (all lanes call it)
+        auto count_of = [&](int b, int c, bool live) -> uint32_t {
+            if (Bk <= 32) return __shfl_sync(0xffffffffu, hv, (b * k + c) & 31);
+            return live ? hr[b * k + c] : 0u;
+        };
+        RowPos pos;
+        pos.init(lane, csj);
+        for (int i0 = 0; i0 < B * csj; i0 += 32, pos.step(32, csj)) {
+            const int i = i0 + lane;
+            const bool live = i < B * csj && pos.s < cj;
+            const uint64_t *ar = prev + (int64_t)pos.b * prev_s * Lp;
             Wide<Ld> acc;
             wzero(acc);
-            if (S < cj) {
-                const int Lp = j == 0 ? Lf : Ld;  // limbs of the rows read
-                const uint64_t *ar = prev + b * prev_s * Lp;
-                const uint32_t *hb = hr + b * k;
-                for (int q = 0; q < hj; q++) {
-                    const uint32_t pq = __ldg(pt + q * cj + S);
-                    const uint32_t hc = hb[pq >> 16];
-                    if (hc) {
+            if (sparse) {
+                for (unsigned m = nz; m; m &= m - 1) {
+                    const int c = __ffs(m) - 1;
+                    const uint32_t hc = count_of(pos.b, c, live);
+                    const uint32_t r = live ? rm[pos.s * k + c] : 0xFFFFu;
+                    if (r != 0xFFFFu && hc) {
                         Wide<Ld> a;
 #pragma unroll
-                        for (int l = 0; l < Ld; l++) a.w[l] = l < Lp ? ar[(pq & 0xFFFFu) * Lp + l] : 0;
+                        for (int l = 0; l < Ld; l++) a.w[l] = l < Lp ? ar[(int64_t)r * Lp + l] : 0;
                         wmac_small(acc, a, hc);
                     }
                 }
+            } else {
+                for (int q0 = 0; q0 < hj; q0 += QB) {
+                    uint32_t pq[QB], hc[QB];
+#pragma unroll
+                    for (int t = 0; t < QB; t++) pq[t] = live && q0 + t < hj ? __ldg(pt + (q0 + t) * cj + pos.s) : 0u;
+#pragma unroll
+                    for (int t = 0; t < QB; t++) {
+                        hc[t] = count_of(pos.b, (int)(pq[t] >> 16), live);
+                        if (!(live && q0 + t < hj)) hc[t] = 0;
+                    }
+                    Wide<Ld> a[QB];
+#pragma unroll
+                    for (int t = 0; t < QB; t++)
+#pragma unroll
+                        for (int l = 0; l < Ld; l++)
+                            a[t].w[l] = (hc[t] && l < Lp) ? ar[(int64_t)(pq[t] & 0xFFFFu) * Lp + l] : 0;
+#pragma unroll
+                    for (int t = 0; t < QB; t++)
+                        if (hc[t]) wmac_small(acc, a[t], hc[t]);
+                }
             }
-            wstore(dst + i * Ld, acc);
+            if (i < B * csj) wstore(dst + (int64_t)i * Ld, acc);
         }
         prev = dst;
         prev_s = csj;
@@ -121,47 +182,34 @@ template <int Ls, int Lf, int Ld, int VPT, int NB>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
-                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *__restrict__ add_p,
+                           int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,
                            const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col, uint64_t *out,
                            int64_t out_vs, LeafChain chain, unsigned long long *next)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t R = (int64_t)B * Cps;
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (v >= v1) return;
+    const int R = B * Cps;
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(next, 1ull);
+    int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    while (v < v1) {
+        if (lane == 0) got = atomicAdd(next, 1ull);  // the next vertex, awaited after this one
         const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-        if (e1 - e0 > split) continue;  // heavy vertex: tasks, reduce, select, p = 1 kernels
-        uint64_t *orow = out + (v - v0) * out_vs;
-        const uint8_t *cv = col + v * B;
-        for (int64_t i = lane; i < (int64_t)B * Chs; i += 32) {
-            const int64_t b = i / Chs, S = i - b * Chs;
-            if (S >= Ch || rm_h[S * k + cv[b]] == 0xFFFFu) {
-                Wide<Lf> z;
-                wzero(z);
-                wstore(orow + i * Lf, z);
-            }
-        }
-        for (int64_t base = 0; base < R; base += 32 * VPT) {
-            Wide<Lf> acc[VPT];
+        if (e1 - e0 <= split) {  // heavy vertices: tasks, reduce, select, p = 1 kernels
+            uint64_t *orow = out + (v - v0) * out_vs;
+            const uint8_t *cv = col + v * B;
+            zero_missing<Lf>(orow, B, k, Ch, Chs, rm_h, cv, lane);
+            RowPos pos;
+            pos.init(lane, Cps);
+            for (int base = 0; base < R; base += 32 * VPT) {
+                Wide<Lf> acc[VPT];
 #pragma unroll
-            for (int q = 0; q < VPT; q++) wzero(acc[q]);
-            accumulate_rows<Ls, Lf, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
-#pragma unroll
-            for (int q = 0; q < VPT; q++) {
-                const int64_t c = base + q * 32 + lane;
-                if (c < R) {
-                    const int64_t b = c / Cps, T = c - b * Cps;
-                    if (T < Cp) {
-                        const uint32_t d = add_p[T * k + cv[b]];
-                        if (d != 0xFFFFu) wstore(orow + (b * Chs + d) * Lf, acc[q]);
-                    }
-                }
+                for (int q = 0; q < VPT; q++) wzero(acc[q]);
+                accumulate_rows<Ls, Lf, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+                scatter_sums<Lf, VPT>(orow, acc, base, R, Cp, Cps, Chs, k, add_p, cv, pos, lane);
             }
+            leaf_steps<Ld, Lf>(v, v0, orow, Chs, chain, B, k, lane);
         }
-        leaf_steps<Ld, Lf>(v, v0, orow, Chs, chain, B, k, lane);
+        v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 
@@ -170,17 +218,17 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
 template <int Ld>
 __global__ void __launch_bounds__(kWarps * 32)
 leaf_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr, int B, int k,
-                  const uint64_t *out0, int64_t out_vs, int64_t Chs, LeafChain chain,
-                  unsigned long long *next)
+                  const uint64_t *out0, int64_t out_vs, int Chs, LeafChain chain, unsigned long long *next)
 {
     const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned long long got = 0;
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(next, 1ull);
+    int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    while (v < v1) {
         if (lane == 0) got = atomicAdd(next, 1ull);
-        const int64_t v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (v >= v1) return;
-        if (row_ptr[v + 1] - row_ptr[v] > split) continue;  // heavy: the p = 1 kernels
-        leaf_steps<Ld>(v, v0, out0 + (v - v0) * out_vs, Chs, chain, B, k, lane);
+        if (row_ptr[v + 1] - row_ptr[v] <= split)  // heavy: the p = 1 kernels
+            leaf_steps<Ld>(v, v0, out0 + (v - v0) * out_vs, Chs, chain, B, k, lane);
+        v = v0 + (int64_t)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 

@@ -115,6 +115,27 @@ __device__ __forceinline__ void gather_row_range(const int32_t *__restrict__ col
     }
 }
 
+// Position (b, s) of the flat index i = b * stride + s in a vertex's rows (B
+// colourings of `stride` entries each), moved forward without a division per
+// entry: one 32-bit division to start, then steps of the 32 entries a warp
+// covers per sweep.  Row sizes stay below 2^31 (B <= 64, stride <= 12870).
+struct RowPos {
+    int b, s;
+    __device__ __forceinline__ void init(int i, int stride)
+    {
+        b = i / stride;
+        s = i - b * stride;
+    }
+    __device__ __forceinline__ void step(int d, int stride)
+    {
+        s += d;
+        while (s >= stride) {
+            s -= stride;
+            b++;
+        }
+    }
+};
+
 // Width of one of nch column segments of a row of R values: a multiple of the
 // 32 * VPT values a warp covers per sweep.
 template <int VPT>

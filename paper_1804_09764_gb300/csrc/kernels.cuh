@@ -145,7 +145,8 @@ struct LeafChain {
     int n;                       // number of p = 1 steps after the fused step (<= 15)
     int h[15];
     int64_t Ch[15], Chs[15], vs[15];
-    const uint32_t *pairs[15];   // (h, h-1) split tables
+    const uint32_t *pairs[15];   // (h, h-1) split tables (the heavy vertices' p = 1 kernels)
+    const uint16_t *rm[15];      // rank of S \ {c} per (S, c) of size h, 0xFFFF when c is not in S
     const uint32_t *hist[15];    // colour histograms of the leaf's label (or of all neighbours)
     uint64_t *out[15];
 };

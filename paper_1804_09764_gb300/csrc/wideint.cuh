@@ -20,23 +20,31 @@ __device__ __forceinline__ void wzero(Wide<L> &x)
     for (int i = 0; i < L; i++) x.w[i] = 0;
 }
 
-// acc += x (mod 2^(64 L))
+// acc += x (mod 2^(64 L)): one add-with-carry chain over the limbs
 template <int L>
 __device__ __forceinline__ void wadd(Wide<L> &acc, const Wide<L> &x)
 {
     if constexpr (L == 1) {
         acc.w[0] += x.w[0];
+    } else if constexpr (L == 2) {
+        asm("add.cc.u64 %0, %0, %2;\n\t"
+            "addc.u64 %1, %1, %3;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1])
+            : "l"(x.w[0]), "l"(x.w[1]));
+    } else if constexpr (L == 3) {
+        asm("add.cc.u64 %0, %0, %3;\n\t"
+            "addc.cc.u64 %1, %1, %4;\n\t"
+            "addc.u64 %2, %2, %5;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1]), "+l"(acc.w[2])
+            : "l"(x.w[0]), "l"(x.w[1]), "l"(x.w[2]));
     } else {
-        uint64_t c = 0;
-#pragma unroll
-        for (int i = 0; i < L; i++) {
-            uint64_t t = acc.w[i] + x.w[i];
-            uint64_t c1 = t < x.w[i];
-            uint64_t s = t + c;
-            c1 += s < c;
-            acc.w[i] = s;
-            c = c1;
-        }
+        static_assert(L == 4, "1 to 4 limbs");
+        asm("add.cc.u64 %0, %0, %4;\n\t"
+            "addc.cc.u64 %1, %1, %5;\n\t"
+            "addc.cc.u64 %2, %2, %6;\n\t"
+            "addc.u64 %3, %3, %7;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1]), "+l"(acc.w[2]), "+l"(acc.w[3])
+            : "l"(x.w[0]), "l"(x.w[1]), "l"(x.w[2]), "l"(x.w[3]));
     }
 }
 
@@ -68,7 +76,6 @@ __device__ __forceinline__ void wmac(Wide<L> &acc, const Wide<L> &a, const Wide<
     }
 }
 
-// acc += a * s for a small multiplier s (< 2^32 in use: colour histogram counts)
 // acc += a * b mod 2^(64 L) for an La-limb a and an Lb-limb b (La, Lb <= L):
 // schoolbook over the La x Lb limb products that land below limb L; the carry
 // out of row i goes to limb i + Lb (still zero), or is dropped at limb L.
@@ -101,23 +108,40 @@ __device__ __forceinline__ void wmac_mixed(Wide<L> &acc, const Wide<La> &a, cons
     }
 }
 
+// acc += a * s (mod 2^(64 L)) for a one-limb multiplier s (in use: colour
+// histogram counts)
 template <int L>
 __device__ __forceinline__ void wmac_small(Wide<L> &acc, const Wide<L> &a, uint64_t s)
 {
+    // the low halves of a_i * s go into limb i, the high halves into limb i + 1:
+    // two add-with-carry chains of multiply-adds
     if constexpr (L == 1) {
         acc.w[0] += a.w[0] * s;
+    } else if constexpr (L == 2) {
+        asm("mad.lo.cc.u64 %0, %2, %4, %0;\n\t"
+            "madc.lo.u64 %1, %3, %4, %1;\n\t"
+            "mad.hi.u64 %1, %2, %4, %1;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1])
+            : "l"(a.w[0]), "l"(a.w[1]), "l"(s));
+    } else if constexpr (L == 3) {
+        asm("mad.lo.cc.u64 %0, %3, %6, %0;\n\t"
+            "madc.lo.cc.u64 %1, %4, %6, %1;\n\t"
+            "madc.lo.u64 %2, %5, %6, %2;\n\t"
+            "mad.hi.cc.u64 %1, %3, %6, %1;\n\t"
+            "madc.hi.u64 %2, %4, %6, %2;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1]), "+l"(acc.w[2])
+            : "l"(a.w[0]), "l"(a.w[1]), "l"(a.w[2]), "l"(s));
     } else {
-        Wide<L> p;
-        uint64_t carry = 0;
-#pragma unroll
-        for (int i = 0; i < L; i++) {
-            uint64_t lo = a.w[i] * s;
-            uint64_t hi = __umul64hi(a.w[i], s);
-            uint64_t t = lo + carry;
-            carry = hi + (t < lo);
-            p.w[i] = t;
-        }
-        wadd(acc, p);
+        static_assert(L == 4, "1 to 4 limbs");
+        asm("mad.lo.cc.u64 %0, %4, %8, %0;\n\t"
+            "madc.lo.cc.u64 %1, %5, %8, %1;\n\t"
+            "madc.lo.cc.u64 %2, %6, %8, %2;\n\t"
+            "madc.lo.u64 %3, %7, %8, %3;\n\t"
+            "mad.hi.cc.u64 %1, %4, %8, %1;\n\t"
+            "madc.hi.cc.u64 %2, %5, %8, %2;\n\t"
+            "madc.hi.u64 %3, %6, %8, %3;"
+            : "+l"(acc.w[0]), "+l"(acc.w[1]), "+l"(acc.w[2]), "+l"(acc.w[3])
+            : "l"(a.w[0]), "l"(a.w[1]), "l"(a.w[2]), "l"(a.w[3]), "l"(s));
     }
 }
 
