@@ -44,6 +44,8 @@ WORKLOADS = {
     # small case of the same kernels for profiler captures (tables ~4 GB, above L2;
     # root 1, the planner's root for the scale-22 headline)
     "rmat18_tree12": dict(graph=("rmat", 18, 18), template="tree12", root=1, n_iter=1, budget=16 << 30),
+    # smaller still, for full-section captures (tables ~2 GB, one vertex block)
+    "rmat17_tree12": dict(graph=("rmat", 17, 17), template="tree12", root=1, n_iter=1, budget=8 << 30),
     "rmat24_spider15": dict(graph=("rmat", 24, 24), template="spider15", root=0, n_iter=4, budget=150 << 30),
     # labelled templates: 4 seeded labels on graph and template vertices
     "rmat22_tree12_labelled": dict(graph=("rmat", 22, 22), template="tree12", root=-1, n_iter=16,
@@ -76,6 +78,22 @@ def max_over_ranks(x: float, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_check(per_rank, recount, rank0=0):
+    """Cross-check of colouring replicas: per_rank[r] is rank r's list of
+    (colouring index, count) pairs.  Colourings are independent and counts
+    exact, so a count must not depend on the rank that computed it: rank 0
+    recounts the first colouring of every other rank (recount(j) -> count) and
+    compares.  Returns {"checked": n, "equal": bool, "colourings": total}."""
+    checked, equal = 0, True
+    for r, pairs in enumerate(per_rank):
+        if r == rank0 or not pairs:
+            continue
+        j, cnt = pairs[0]
+        checked += 1
+        equal &= recount(j) == cnt
+    return {"checked": checked, "equal": bool(equal), "colourings": sum(len(p) for p in per_rank)}
 
 
 def kernel_source_digest() -> str:
@@ -203,25 +221,67 @@ def oracle_sample(wl, target_s=15.0, max_scale=None):
         g, k, e, root
 
 
+_WORKER_GRAPHS = {}
+
+
+def _oracle_colouring(spec, k, e, root, seed, j):
+    """One oracle colouring in a worker process (imports oracle there; the
+    graph is generated once per process, outside the timed calls)."""
+    import oracle as O
+
+    if spec not in _WORKER_GRAPHS:
+        _WORKER_GRAPHS[spec] = make_graph(spec)
+    t = time.perf_counter()
+    O.count_maps(_WORKER_GRAPHS[spec], k, e, root, seed=seed, j=j)
+    return time.perf_counter() - t
+
+
+def oracle_cores_rate(g_spec, k, e, root, U_per_colouring, colourings, cores):
+    """The oracle on the host's cores: independent colourings (Algorithm 1's
+    outer loop) in `cores` single-threaded worker processes, started with
+    spawn (a process forked after CUDA initialisation would hang).  Returns
+    (updates/s over the wall time of the batch, wall seconds)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_colouring, [g_spec] * cores, [k] * cores, [e] * cores, [root] * cores,
+                    [1] * cores, range(1000, 1000 + cores)))  # start-up and graph build, untimed
+        t = time.perf_counter()
+        list(ex.map(_oracle_colouring, [g_spec] * colourings, [k] * colourings, [e] * colourings,
+                    [root] * colourings, [1] * colourings, range(colourings)))
+        wall = time.perf_counter() - t
+    return U_per_colouring * colourings / wall, wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
-    s, dt, desc, g, k, e, root = oracle_sample(wl, target_s=args.ref_seconds)
+    s, dt, desc, g, k, e, root = oracle_sample(wl, target_s=args.ref_seconds / 4)
     U = plan_updates_host(g, k, e, root)
+    cores = host_cores()
+    spec = wl["graph"] if s is None else ("rmat", s, wl["graph"][2])
+    # each step: one colouring per host core, in parallel (a bounded sample)
     steps = []
-    import oracle as O
     for i in range(args.steps):
-        t = time.perf_counter()
-        O.count_maps(g, k, e, root, seed=1, j=i + 1)
-        steps.append(time.perf_counter() - t)
+        rate, wall = oracle_cores_rate(spec, k, e, root, U, cores, cores)
+        steps.append(wall)
     tot = sum(steps)
-    value = U * len(steps) / tot
+    value = U * cores * len(steps) / tot
+    desc += f"; one colouring per core on {cores} cores per step"
     line = {"impl": "reference", "metric": "edge_colourset_updates_per_s", "value": value,
             "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u256", "data": "synthetic",
             "config": {"workload": args.workload, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -257,12 +317,33 @@ def plan_updates_host(g, k, e, root):
     return U
 
 
+def fifo_latencies(arrivals, service):
+    """Arrival-to-result latencies of one server taking requests in arrival
+    order: request i starts when it has arrived and request i - 1 is done."""
+    done, out = 0.0, []
+    for a, sv in zip(arrivals, service):
+        done = max(done, a) + sv
+        out.append(done - a)
+    return out
+
+
+def pctl(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * (len(xs) - 1) + 0.5))] if xs else None
+
+
 def run_serving(args):
-    """Continuous-batching serving run: resident R-MAT graphs (scales 16..max)
-    plus an Erdos-Renyi graph (n = 1M, degree 16); requests with Poisson
-    arrivals, each a uniform labelled tree (Pruefer) with k in 5..12 and 1..16
-    colourings.  Reports p50/p99 latency (arrival to result) and throughput, and
-    the same requests run one after another through cc_count (plain path)."""
+    """Continuous-batching serving: resident R-MAT graphs (scales 16..max) plus
+    an Erdos-Renyi graph (n = 2^20, degree 16); requests with Poisson arrivals,
+    each a uniform labelled tree (Pruefer sequence) with k in 5..12 and 1..16
+    colourings.  The served run submits every request at its arrival time and
+    reports p50/p99 latency (arrival to result) and throughput.  The same
+    requests are also run one after another, on the same GPU, in two plain
+    forms: through cc_count (each request's colourings batched into passes) and
+    with one colouring per pass; their latencies under the same arrivals are
+    those of a single FIFO server with the measured service times.  A second,
+    lighter arrival rate (a sustainable load) is served as well.  Every served
+    result must equal the plain results."""
     import torch
 
     from paper_1804_09764_gb300 import build as B
@@ -274,65 +355,120 @@ def run_serving(args):
     graphs = [gg.rmat_graph(sc, seed=sc) for sc in scales] + [gg.er_graph(1 << 20, 16, seed=7)]
     budget = min(int(args.budget_gb * (1 << 30)) if args.budget_gb else 250 << 30,
                  int(torch.cuda.mem_get_info(0)[0] * 0.9))
-    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
-    gids = [ctx.graph_load(g) for g in graphs]
-    reqs = []
-    t = 0.0
-    for i in range(args.requests):
-        t += rng.exponential(1.0 / args.rate)
-        k = int(rng.integers(5, 13))
-        e = gg.prufer_tree(k, 10_000 + i)
-        reqs.append(dict(at=t, g=int(rng.integers(0, len(graphs))), k=k, e=e, n_iter=int(rng.integers(1, 17)),
-                         seed=int(rng.integers(0, 2 ** 40))))
-    for r in reqs:
-        r["tid"] = ctx.template_load(r["k"], r["e"])
-    # updates per request (same U definition as the counting metric)
+
+    def make_requests(n, rate, seed0):
+        r_rng = np.random.default_rng(seed0)
+        out, t = [], 0.0
+        for i in range(n):
+            t += r_rng.exponential(1.0 / rate)
+            k = int(r_rng.integers(5, 13))
+            out.append(dict(at=t, g=int(r_rng.integers(0, len(graphs))), k=k, e=gg.prufer_tree(k, seed0 * 100_000 + i),
+                            n_iter=int(r_rng.integers(1, 17)), seed=int(r_rng.integers(0, 2 ** 40))))
+        return out
+
+    def served(ctx, gids, reqs):
+        for r in reqs:
+            r["tid"] = ctx.template_load(r["k"], r["e"])
+        torch.cuda.synchronize()
+        start = time.perf_counter()
+        ids = []
+        for r in reqs:
+            now = time.perf_counter() - start
+            if r["at"] > now:
+                time.sleep(r["at"] - now)
+            ids.append((ctx.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"]), r))
+        for rid, r in ids:
+            try:
+                r["served"] = ctx.wait(rid, r["n_iter"], timeout_s=7200)["counts"]
+            except cc.CCError as e:
+                r["served"] = e.status
+        return time.perf_counter() - start, ctx.serve_stats()
+
+    def plain(ctx, gids, reqs, key):
+        # one request after another; the service time of each, and its result
+        for r in reqs:
+            tid = ctx.template_load(r["k"], r["e"])
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            try:
+                r[key] = ctx.count(gids[r["g"]], tid, seed=r["seed"], n_iter=r["n_iter"])["counts"]
+            except cc.CCError as e:
+                r[key] = e.status
+            r[key + "_s"] = time.perf_counter() - t
+            ctx.template_free(tid)
+
+    reqs = make_requests(args.requests, args.rate, 2024)
     for r in reqs:
         r["U"] = plan_updates_host(graphs[r["g"]], r["k"], r["e"], 0) * r["n_iter"]
-    # plain path: one request after another through cc_count; a request whose
-    # tables cannot fit the budget is refused (CC_ERR_BUDGET) on both paths
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in reqs:
-        try:
-            r["plain"] = ctx.count(gids[r["g"]], r["tid"], seed=r["seed"], n_iter=r["n_iter"])["counts"]
-        except cc.CCError as e:
-            r["plain"] = e.status
-    plain_s = time.perf_counter() - t0
-    # served: submit at arrival times, collect results
-    start = time.perf_counter()
-    ids = []
-    for r in reqs:
-        now = time.perf_counter() - start
-        if r["at"] > now:
-            time.sleep(r["at"] - now)
-        ids.append((ctx.submit(gids[r["g"]], r["tid"], r["seed"], r["n_iter"]), r))
-    mismatched = 0
-    for rid, r in ids:
-        try:
-            got = ctx.wait(rid, r["n_iter"], timeout_s=3600)["counts"]
-        except cc.CCError as e:
-            got = e.status
-        mismatched += got != r["plain"]
-    served_s = time.perf_counter() - start
-    st = ctx.serve_stats()
+    # served at the offered rate
+    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
+    gids = [ctx.graph_load(g) for g in graphs]
+    with ClockSampler(0) as clk:
+        served_s, st = served(ctx, gids, reqs)
+    # the same requests, one after another: batched passes, then one colouring per pass
+    plain(ctx, gids, reqs, "plain")
+    ctx.close()
+    ctx1 = cc.Context(budget_bytes=budget, batch=1, autotune=0)
+    gids1 = [ctx1.graph_load(g) for g in graphs]
+    plain(ctx1, gids1, reqs, "one")
+    ctx1.close()
     ok = [r for r in reqs if not isinstance(r["plain"], int)]
     U = sum(r["U"] for r in ok)
+    arrivals = [r["at"] for r in reqs]
+
+    def plain_summary(key):
+        lat = fifo_latencies(arrivals, [r[key + "_s"] for r in reqs])
+        busy = sum(r[key + "_s"] for r in reqs)
+        return {"busy_s": busy, "requests_per_s_busy": len(reqs) / busy, "updates_per_s_busy": U / busy,
+                "p50_latency_s": pctl(lat, 0.5), "p99_latency_s": pctl(lat, 0.99),
+                "makespan_s": max(a + l for a, l in zip(arrivals, lat))}
+
+    differ = sum(r["served"] != r["plain"] for r in reqs) + sum(r["one"] != r["plain"] for r in ok)
+
+    def brief(x):
+        return x if isinstance(x, int) else [len(x), x[0] if x else None]
+
+    mismatches = [{"i": i, "graph": graphs[r["g"]].name, "k": r["k"], "n_iter": r["n_iter"],
+                   "served": brief(r["served"]), "plain": brief(r["plain"]), "one": brief(r["one"]),
+                   "first_differing": next((j for j, (a, b) in enumerate(zip(r["served"], r["plain"])) if a != b), None)
+                   if not isinstance(r["served"], int) and not isinstance(r["plain"], int) else None}
+                  for i, r in enumerate(reqs) if r["served"] != r["plain"] or r["one"] != r["plain"]][:12]
+    # a sustainable load: fewer, sparser requests, served only (the plain forms'
+    # service times do not depend on the rate)
+    light = make_requests(args.light_requests, args.light_rate, 4048)
+    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
+    gids = [ctx.graph_load(g) for g in graphs]
+    light_s, st_l = served(ctx, gids, light)
+    plain(ctx, gids, light, "plain")
+    ctx.close()
+    light_ok = [r for r in light if not isinstance(r["plain"], int)]
+    differ += sum(r["served"] != r["plain"] for r in light)
+    lat_l = fifo_latencies([r["at"] for r in light], [r["plain_s"] for r in light])
     line = {"metric": "served_p99_latency_s", "value": st["p99_latency_s"], "unit": "s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": served_s * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64/u128/u192", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u64..u256", "data": "synthetic",
             "config": {"workload": "serve", "graphs": [g.name for g in graphs], "requests": args.requests,
-                       "rate_per_s": args.rate, "slots": args.serve_slots, "k": "5..12", "colourings": "1..16",
-                       "arrival_span_s": reqs[-1]["at"]},
+                       "rate_per_s": args.rate, "slots": args.serve_slots, "batch_cap": 16, "k": "5..12",
+                       "colourings": "1..16", "arrival_span_s": arrivals[-1]},
             "serving": {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
                         "mean_latency_s": st["mean_latency_s"], "completed": st["completed"],
-                        "requests_per_s": args.requests / served_s, "updates_per_s": U / served_s,
+                        "requests_per_s": st["completed"] / served_s, "updates_per_s": U / served_s,
                         "busy_s": st["busy_seconds"], "admissions_deferred": st["admissions_deferred"],
-                        "refused_over_budget": len(reqs) - len(ok), "results_differ_from_plain": mismatched},
-            "plain_sequential": {"seconds": plain_s, "requests_per_s": args.requests / plain_s,
-                                 "updates_per_s": U / plain_s}}
+                        "passes": st["passes"], "shared_passes": st["shared_passes"],
+                        "colourings_run": st["colourings_run"],
+                        "refused_over_budget": len(reqs) - len(ok), "results_differ_from_plain": differ,
+                        "mismatches": mismatches},
+            "plain_sequential": plain_summary("plain"),
+            "one_colouring_per_launch": plain_summary("one"),
+            "sustainable": {"requests": len(light), "rate_per_s": args.light_rate,
+                            "served_p50_latency_s": st_l["p50_latency_s"], "served_p99_latency_s": st_l["p99_latency_s"],
+                            "served_requests_per_s": st_l["completed"] / light_s,
+                            "shared_passes": st_l["shared_passes"], "passes": st_l["passes"],
+                            "plain_sequential_p50_latency_s": pctl(lat_l, 0.5),
+                            "plain_sequential_p99_latency_s": pctl(lat_l, 0.99),
+                            "refused_over_budget": len(light) - len(light_ok)},
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def run_multi(args):
@@ -382,6 +518,137 @@ def run_multi(args):
     ctx.close()
 
 
+def run_graph_batch(args):
+    """Many small graphs in one launch: N Erdos-Renyi graphs of the tiny
+    workload's shape (n = 2000, average degree 8, each its own seed) with the
+    5-vertex path, one colouring each, counted as one resident batch
+    (cc_graph_load_batch + cc_count_batch: every DP launch covers all N) and
+    as N separate counts of the same graphs (one graph per launch).  Per-graph
+    counts must be identical."""
+    import torch
+
+    from paper_1804_09764_gb300 import build as B
+    from paper_1804_09764_gb300 import cc
+
+    B.build()
+    n_graphs = args.graphs
+    gs = [gg.er_graph(2000, 8, seed=1000 + i) for i in range(n_graphs)]
+    k, e = gg.template_edges("P5")
+    n_iter = args.n_iter or 1
+    ctx = cc.Context(budget_bytes=8 << 30, batch=16, timing=0)
+    bid = ctx.graph_load_batch(gs)
+    gids = [ctx.graph_load(g) for g in gs]
+    tid = ctx.template_load(k, e, 2)
+    U = sum(plan_updates_host(g, k, e, 2) for g in gs) * n_iter
+    for i in range(args.warmup):
+        ctx.count_batch(bid, tid, seed=77, n_iter=n_iter, first_iter=i * n_iter)
+        for gi in gids:
+            ctx.count(gi, tid, seed=77, n_iter=n_iter, first_iter=i * n_iter)
+    bat_dev = bat_wall = sep_dev = sep_wall = 0.0
+    bat_l = sep_l = 0
+    differ = 0
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = ctx.count_batch(bid, tid, seed=4321, n_iter=n_iter, first_iter=i * n_iter)
+            bat_wall += time.perf_counter() - t
+            bat_dev += r["device_seconds"]
+            bat_l += r["kernel_launches"]
+            t = time.perf_counter()
+            for gi, gid in enumerate(gids):
+                a = ctx.count(gid, tid, seed=4321, n_iter=n_iter, first_iter=i * n_iter)
+                sep_dev += a["device_seconds"]
+                sep_l += a["kernel_launches"]
+                differ += a["counts"] != r["counts"][gi]
+            sep_wall += time.perf_counter() - t
+    per = n_graphs * args.steps
+    line = {"metric": "edge_colourset_updates_per_s", "value": U * args.steps / bat_dev, "unit": "updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * bat_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "er2000_p5_batch", "graphs_per_launch": n_graphs, "n_per_graph": 2000,
+                       "avg_degree": 8, "template": "P5", "colourings_per_graph": n_iter,
+                       "l2": "inputs smaller than L2 (launch-bound workload)"},
+            "graph_batch": {"batched_us_per_graph": 1e6 * bat_dev / per, "separate_us_per_graph": 1e6 * sep_dev / per,
+                            "batched_wall_us_per_graph": 1e6 * bat_wall / per,
+                            "separate_wall_us_per_graph": 1e6 * sep_wall / per,
+                            "speedup_device": sep_dev / bat_dev, "speedup_wall": sep_wall / bat_wall,
+                            "launches_batched_per_step": bat_l / args.steps,
+                            "launches_separate_per_step": sep_l / args.steps, "results_differ": differ},
+            "gpu_launches": int(bat_l), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_compare_plain(args):
+    """The batched form against the plain one-colouring-per-launch form on the
+    same GPU, graph, template and colourings (the default workload here is
+    R-MAT scale 20 / caterpillar-10, 64 colourings).  Plain: one colouring per
+    pass, gather and combine as separate launches for every DP stage, no CUDA
+    graph, no autotuning.  Batched: as many colourings per pass as the budget
+    holds (at most 16), fused gather + combine kernels, every pass replayed
+    from a captured CUDA graph, and the shape (split threshold, column
+    segments, vertex-block size) chosen by the autotuner on the first count.
+    The counts of the two forms must be identical."""
+    import torch
+
+    from paper_1804_09764_gb300 import build as B
+    from paper_1804_09764_gb300 import cc
+
+    B.build()
+    wl = dict(WORKLOADS[args.workload])
+    n_iter = args.n_iter or wl["n_iter"]
+    g = make_graph(wl["graph"])
+    k, e = gg.template_edges(wl["template"])
+    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else wl["budget"]
+    budget = min(budget, int(torch.cuda.mem_get_info(0)[0] * 0.9))
+    forms = {"plain": dict(batch=1, fused=0, use_cuda_graph=0, autotune=0),
+             "batched": dict(batch=0, fused=1, use_cuda_graph=1, autotune=1)}
+    out, counts = {}, {}
+    for name, opt in forms.items():
+        # no per-kernel timing (it keeps passes out of CUDA graphs): device time
+        # is the CUDA-event span of each count's passes on the context's stream
+        ctx = cc.Context(budget_bytes=budget, timing=0, **opt)
+        gid = ctx.graph_load(g)
+        tid = ctx.template_load(k, e, wl["root"])
+        for i in range(args.warmup):  # the batched form tunes and captures here
+            ctx.count(gid, tid, seed=4242, n_iter=n_iter, first_iter=i * n_iter)
+        dev = wall = 0.0
+        launches = 0
+        got = []
+        with ClockSampler(0) as clk:
+            for i in range(args.steps):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                r = ctx.count(gid, tid, seed=12345, n_iter=n_iter, first_iter=i * n_iter)
+                wall += time.perf_counter() - t
+                dev += r["device_seconds"]
+                launches += r["kernel_launches"]
+                got.append(r["counts"])
+        info = ctx.plan_info(gid, tid)
+        U = info["updates_per_colouring"] * n_iter * args.steps
+        out[name] = {"value": U / dev, "ms_per_step": 1e3 * dev / args.steps,
+                     "wall_ms_per_step": 1e3 * wall / args.steps, "gpu_launches_per_step": launches / args.steps,
+                     "options": opt, "batch": info["batch"], "passes_per_step": -(-n_iter // info["batch"]),
+                     "split_threshold": info["split_threshold"], "col_chunks": info.get("col_chunks"),
+                     "blocks": info["n_blocks"], "block_vertices": info["block_vertices"],
+                     "workspace_gb": info["workspace_bytes"] / 1e9,
+                     "clocks": clk.summary()}
+        counts[name] = got
+        ctx.close()
+    pl, bt = out["plain"], out["batched"]
+    line = {"metric": "edge_colourset_updates_per_s", "value": bt["value"], "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": bt["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64..u128",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "template": wl["template"],
+                       "k": k, "colourings_per_step": n_iter, "l2": "inputs larger than L2"},
+            "compare_plain": {"plain": pl, "batched": bt, "speedup": bt["value"] / pl["value"],
+                              "identical_counts": counts["plain"] == counts["batched"]},
+            "gpu_launches": int(bt["gpu_launches_per_step"] * args.steps), "clocks": bt["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,12 +671,21 @@ def main():
     ap.add_argument("--vertex-order", type=int, default=0, help="0: by decreasing degree, 1: input order")
     ap.add_argument("--multi", action="store_true",
                     help="graphlet-frequency run: all 11 trees on 7 vertices, merged vs one count each")
+    ap.add_argument("--l2-persist-mb", type=int, default=0,
+                    help="MiB of L2 kept for the hub rows of each gathered table (0: none)")
     ap.add_argument("--col-chunks", type=int, default=0,
                     help="column segments per neighbour row in the persistent gathers (0: one warp sweep each, "
                          "whole rows in the fused kernels; 1: whole rows)")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--graph-batch", action="store_true",
+                    help="many small graphs in one launch against one graph per count")
+    ap.add_argument("--graphs", type=int, default=1000, help="graphs of the --graph-batch run")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="batched + CUDA graph + autotuned form against one colouring per pass, unfused, no graph")
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--light-requests", type=int, default=300, help="requests of the sustainable-rate serving run")
+    ap.add_argument("--light-rate", type=float, default=4.0, help="arrival rate of the sustainable-rate serving run")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-max-scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
@@ -429,6 +705,16 @@ def main():
     if args.multi:
         if rank == 0:
             run_multi(args)
+        return
+    if args.graph_batch:
+        if rank == 0:
+            run_graph_batch(args)
+        return
+    if args.compare_plain:
+        if args.workload == DEFAULT:
+            args.workload = "rmat20_caterpillar10"
+        if rank == 0:
+            run_compare_plain(args)
         return
 
     import torch
@@ -453,7 +739,8 @@ def main():
     budget = min(budget, int(torch.cuda.mem_get_info(local)[0] * 0.9))
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
                      block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused,
-                     autotune=args.autotune, vertex_order=args.vertex_order, col_chunks=args.col_chunks)
+                     autotune=args.autotune, vertex_order=args.vertex_order, col_chunks=args.col_chunks,
+                     l2_persist_mb=args.l2_persist_mb)
     gid = ctx.graph_load(g)
     tlab = glab = None
     if wl.get("labels"):
@@ -475,12 +762,15 @@ def main():
         torch.distributed.barrier()
     dev_s = 0.0
     launches = 0
+    mine = []  # (colouring index, count) of the timed steps
     with ClockSampler(local) as clk:
         t_start = time.perf_counter()
         for i in range(args.steps):
             r = step(args.warmup + i)
             dev_s += r["device_seconds"]
             launches += r["kernel_launches"]
+            j0 = replica_first_iter(rank, world, args.warmup + i, n_iter)
+            mine.extend((j0 + b, c) for b, c in enumerate(r["counts"]))
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -489,8 +779,14 @@ def main():
     insts = ctx.kernel_instances()  # the timed steps only (before the end-to-end counts)
     info = ctx.plan_info(gid, tid)  # the plan the timed counts used
     elapsed = dev_s
+    rcheck = None
     if world > 1:
         elapsed = max_over_ranks(elapsed, device=f"cuda:{local}")
+        per_rank = [None] * world
+        torch.distributed.all_gather_object(per_rank, mine)
+        if rank == 0:
+            rcheck = replica_check(per_rank, lambda j: ctx.count(gid, tid, seed=12345, n_iter=1,
+                                                                 first_iter=j)["counts"][0])
     U = info["updates_per_colouring"] * n_iter * args.steps * world
     value = U / elapsed
 
@@ -555,10 +851,17 @@ def main():
                          "dram_achieved": None, "dram_frac": None})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        s, dt, desc, gs, k2, e2, root2 = oracle_sample(wl, target_s=15.0)
+        # a bounded sample: the oracle on an R-MAT graph of the workload's
+        # parameters whose one colouring takes a few seconds, one colouring per
+        # host core in parallel
+        s, dt, desc, gs, k2, e2, root2 = oracle_sample(wl, target_s=12.0)
         Us = plan_updates_host(gs, k2, e2, root2)
-        cpu = {"value": Us / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-               "sample": desc + f", {dt:.1f} s"}
+        cores = host_cores()
+        spec = wl["graph"] if s is None else ("rmat", s, wl["graph"][2])
+        rate, wall = oracle_cores_rate(spec, k2, e2, root2, Us, cores, cores)
+        cpu = {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": desc + f"; {cores} colourings, one per core, in {wall:.1f} s",
+               "single_core": {"value": Us / dt, "seconds": round(dt, 2)}}
     line = {
         "metric": "edge_colourset_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -574,13 +877,14 @@ def main():
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
                    "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused), "autotune": bool(args.autotune),
                    "vertex_order": "degree" if args.vertex_order == 0 else "input",
-                   "col_chunks": args.col_chunks or "auto",
+                   "col_chunks": args.col_chunks or "auto", "l2_persist_mb": args.l2_persist_mb,
                    "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row, 4 rows in flight",
                               2: "warp (16-byte vectors)", 3: "group (row per 32-256 threads)",
                               4: "persistent warp + L2 prefetch", 5: "warp per row, one pass",
                               6: "persistent warp per row, 2 rows in flight"}[args.gather_mode]},
         "hbm_frac_step": info["algorithmic_bytes_per_colouring"] * n_iter * args.steps / elapsed / 1e9 / peak,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "replica_check": rcheck,
         "clocks": clk.summary(),
         "kernels": {k_: {"launches": v["launches"], "ms": round(1e3 * v["seconds"], 3),
                          "GBps": (v["bytes"] / v["seconds"] / 1e9) if v["seconds"] else None,

@@ -91,7 +91,7 @@ typedef struct cc_options {
                                   decides.  On the first pass of every plan, each gather site
                                   times its kernel variants (gather_mode values, rows in
                                   flight) and keeps the fastest. */
-    int32_t max_slots;         /* serving: requests in flight at once (default 4) */
+    int32_t max_slots;         /* serving: groups (graph, template class) in flight at once (default 4) */
     int32_t timing;            /* 1: record per-kernel CUDA-event times (cc_kernel_stats) */
     int32_t gather_mode;       /* table-gather kernel: 1 (default): warp per row, persistent
                                   warps pulling rows from a counter, 4 neighbour rows in
@@ -109,7 +109,12 @@ typedef struct cc_options {
                                   (at most 16) for the heavy-vertex task gathers and the
                                   unfused gathers, whole rows for the fused gather + select
                                   kernels; n > 0: n segments everywhere (1: whole rows) */
-    int32_t reserved[3];
+    int32_t l2_persist_mb;     /* MiB of L2 set aside (for this context) for the rows read
+                                  most often: before each table gather the stream's access
+                                  window covers the first l2_persist_mb MiB of the source
+                                  table, where degree ordering puts the hub rows (persisting
+                                  hits, streaming misses); 0 (default): no window */
+    int32_t reserved[2];
 } cc_options;
 
 void cc_default_options(cc_options *opt);
@@ -138,6 +143,28 @@ const char *cc_status_string(cc_status s);
 cc_status cc_graph_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr,
                             const int32_t *col_idx, uint32_t flags, cc_graph_id *out);
 cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g);
+
+/*
+ * A batch of many graphs loaded as one: every DP launch of a count then covers
+ * all of them (the batching of many small graphs into one launch; the paper
+ * counts one graph at a time, and its Eq. 1 is local to a vertex's
+ * neighbourhood, so the DP of a disjoint union is the DPs of its parts).
+ *   member_off  host [n_graphs + 1]: member graph i is vertices
+ *               member_off[i] .. member_off[i + 1] - 1 of the CSR; 0 = first,
+ *               n = last, non-decreasing (empty members allowed)
+ *   n, row_ptr, col_idx, flags as cc_graph_load_csr, for the disjoint union
+ *               (vertex ids of the union)
+ * Member i's colours are drawn from its vertices' ids within the member (the
+ * union id minus member_off[i]), so colouring j of a member is the colouring
+ * j it gets when loaded alone and its counts (cc_count_batch) are the counts
+ * of loading it alone, bit for bit.  cc_count and the other entry points take
+ * the batch as one graph: their counts are the sums over the members.
+ * Errors: those of cc_graph_load_csr; CC_ERR_INVALID_ARG (bad offsets);
+ * CC_ERR_BAD_GRAPH also when an edge joins two members (always checked).
+ */
+cc_status cc_graph_load_batch(cc_ctx *ctx, int32_t n_graphs, const int64_t *member_off, int64_t n,
+                              const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                              cc_graph_id *out);
 
 /*
  * Load a tree template T (Section 2.1), k = |V_T| in 1..16.
@@ -222,6 +249,26 @@ typedef struct cc_count_args {
 cc_status cc_count_ex(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_count_args *args,
                       uint64_t *counts, int32_t limbs_capacity, cc_result *res);
 
+/*
+ * cc_count_ex per member graph of a batch (cc_graph_load_batch; a graph loaded
+ * by cc_graph_load_csr is a batch of one).  One pass of the DP covers every
+ * member; only the root sums are kept per member.
+ *   counts     host [n_graphs][n_iter][limbs_capacity]: member i's colourful
+ *              copies (Eq. 3's numerator) per colouring, as cc_count_ex
+ *   estimates  optional host [n_graphs]: member i's estimate (Eq. 3, mean
+ *              over the colourings)
+ *   args       as cc_count_ex; args->maps, if set, is [n_graphs][n_iter][cap];
+ *              sample_maps as cc_count_ex (union ids)
+ *   res        the fields shared by the members; estimate and median_of_means
+ *              hold the batch's total estimate (the sum over members)
+ * Errors as cc_count_ex.
+ */
+cc_status cc_count_batch(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_count_args *args,
+                         uint64_t *counts, int32_t limbs_capacity, double *estimates, cc_result *res);
+
+/* Member graphs of a loaded graph (1 unless loaded by cc_graph_load_batch). */
+cc_status cc_graph_members(cc_ctx *ctx, cc_graph_id g, int32_t *n_graphs);
+
 /* Static description of the plan for (graph, template) under the context options. */
 typedef struct cc_plan_info {
     int32_t k, root, n_chains, n_tables;
@@ -244,6 +291,11 @@ typedef struct cc_plan_info {
     int64_t block_vertices;          /* vertices per streamed block in use */
     int32_t col_chunks;              /* column segments in use (cc_options.col_chunks meaning) */
     int32_t shape_tuned;             /* 1: split, segments and block size come from the autotuner */
+    /* the device memory the same plan would need (at the same batch) if no
+       count table were freed before the end of the pass, if the vertices were
+       not streamed in blocks, and with neither: the one-GPU counterpart of the
+       paper's peak-memory comparison (Section 4.4) of its pipelined schedule (Section 3.2) */
+    uint64_t workspace_no_reuse_bytes, workspace_no_blocks_bytes, workspace_naive_bytes;
 } cc_plan_info;
 
 /* Describes the plan the last cc_count of (g, t) used while it is still
@@ -392,9 +444,16 @@ typedef struct cc_request {
 } cc_request;
 
 /*
- * Submit a request to the continuous-batching loop.  It is admitted when a
- * slot is free and its plan's workspace fits the free arena; admitted requests
- * run concurrently on their own streams, one colouring batch at a time.
+ * Submit a request to the continuous-batching loop.  Admitted requests are
+ * grouped by graph and by template up to isomorphism (isomorphic templates
+ * have the same counts).  A group runs one colouring pass at a time on its own
+ * stream; each pass takes the next pending colourings of all the group's
+ * requests in arrival order, up to cc_options.batch (default 16), so one
+ * launch carries colourings of several requests, and a request joins its
+ * group's next pass as soon as it is admitted.  Up to max_slots groups run
+ * concurrently; a request that needs a new group is admitted when a slot is
+ * free and the group's workspace fits the free arena.  Results are those of
+ * cc_count_ex with the request's seed, first_iter and n_iter.
  */
 cc_status cc_submit(cc_ctx *ctx, const cc_request *req, cc_req_id *out);
 /* CC_PENDING while running; CC_OK with results; an error if it failed.
@@ -410,6 +469,10 @@ typedef struct cc_serve_stats {
     double p50_latency_s, p99_latency_s, mean_latency_s;
     double busy_seconds;           /* wall time with at least one request in flight */
     int64_t admissions_deferred;   /* times a queued request waited for memory or a slot */
+    int64_t passes;                /* colouring passes run */
+    int64_t shared_passes;         /* passes whose launches carried colourings of two or more requests */
+    int64_t colourings_run;        /* colourings computed by those passes */
+    int64_t groups;                /* groups (graph, template class) running now */
 } cc_serve_stats;
 
 cc_status cc_serve_stats_get(cc_ctx *ctx, cc_serve_stats *out);

@@ -52,7 +52,7 @@ class cc_options(ctypes.Structure):
                 ("block_vertices", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("autotune", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
-                ("col_chunks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("col_chunks", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class cc_result(ctypes.Structure):
@@ -93,7 +93,9 @@ class cc_plan_info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_uint64), ("table4_memory", ctypes.c_int64),
                 ("table4_computation", ctypes.c_int64), ("limb_products_per_colouring", ctypes.c_double),
                 ("split_threshold", ctypes.c_int64), ("block_vertices", ctypes.c_int64),
-                ("col_chunks", ctypes.c_int32), ("shape_tuned", ctypes.c_int32)]
+                ("col_chunks", ctypes.c_int32), ("shape_tuned", ctypes.c_int32),
+                ("workspace_no_reuse_bytes", ctypes.c_uint64), ("workspace_no_blocks_bytes", ctypes.c_uint64),
+                ("workspace_naive_bytes", ctypes.c_uint64)]
 
 
 class cc_step_info(ctypes.Structure):
@@ -128,7 +130,8 @@ class cc_serve_stats(ctypes.Structure):
                 ("cancelled", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
                 ("mean_latency_s", ctypes.c_double), ("busy_seconds", ctypes.c_double),
-                ("admissions_deferred", ctypes.c_int64)]
+                ("admissions_deferred", ctypes.c_int64), ("passes", ctypes.c_int64),
+                ("shared_passes", ctypes.c_int64), ("colourings_run", ctypes.c_int64), ("groups", ctypes.c_int64)]
 
 
 _lib = None
@@ -150,6 +153,9 @@ def load_library(path: str = LIB_PATH):
         "cc_last_error": (ctypes.c_char_p, []),
         "cc_status_string": (ctypes.c_char_p, [I32]),
         "cc_graph_load_csr": (I32, [P, I64, P, P, ctypes.c_uint32, P]),
+        "cc_graph_load_batch": (I32, [P, I32, P, I64, P, P, ctypes.c_uint32, P]),
+        "cc_graph_members": (I32, [P, I64, P]),
+        "cc_count_batch": (I32, [P, I64, I64, P, P, I32, P, P]),
         "cc_graph_free": (I32, [P, I64]),
         "cc_template_load": (I32, [P, I32, P, I32, P]),
         "cc_template_free": (I32, [P, I64]),
@@ -274,7 +280,7 @@ class Context:
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
                  fused: int = 1, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
-                 vertex_order: int = 0, col_chunks: int = 0, stream=None):
+                 vertex_order: int = 0, col_chunks: int = 0, l2_persist_mb: int = 0, stream=None):
         import torch
 
         lib = load_library()
@@ -306,6 +312,7 @@ class Context:
         opt.gather_mode = gather_mode
         opt.vertex_order = vertex_order
         opt.col_chunks = col_chunks
+        opt.l2_persist_mb = l2_persist_mb
         torch.cuda.synchronize(device)
         h = ctypes.c_void_p()
         _check(lib.cc_create(ctypes.byref(h), ctypes.byref(opt)))
@@ -344,6 +351,38 @@ class Context:
     def graph_load(self, graph, validate: bool = False) -> int:
         """Load a ``graphgen.CSRGraph``."""
         return self.graph_load_csr(graph.row_ptr, graph.col_idx, graph.n, validate)
+
+    def graph_load_batch(self, graphs, validate: bool = False) -> int:
+        """cc_graph_load_batch: several ``graphgen.CSRGraph`` as one resident
+        disjoint union (member i = graphs[i])."""
+        off = np.zeros(len(graphs) + 1, dtype=np.int64)
+        for i, g in enumerate(graphs):
+            off[i + 1] = off[i] + g.n
+        rp = [np.zeros(1, dtype=np.int64)]
+        ci = []
+        e0 = 0
+        for i, g in enumerate(graphs):
+            rp.append(np.asarray(g.row_ptr[1:], dtype=np.int64) + e0)
+            ci.append(np.asarray(g.col_idx, dtype=np.int64) + off[i])
+            e0 += int(g.row_ptr[-1])
+        rp = np.concatenate(rp)
+        ci = np.concatenate(ci).astype(np.int32) if ci else np.zeros(0, np.int32)
+        return self.graph_load_batch_csr(off, rp, ci, validate)
+
+    def graph_load_batch_csr(self, member_off, row_ptr, col_idx, validate: bool = False) -> int:
+        """cc_graph_load_batch on the union's CSR arrays (host)."""
+        off = np.ascontiguousarray(member_off, dtype=np.int64)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        gid = ctypes.c_int64()
+        _check(self._lib.cc_graph_load_batch(self._h, off.size - 1, _ptr(off), int(off[-1]), _ptr(rp), _ptr(ci),
+                                             CC_VALIDATE if validate else 0, ctypes.byref(gid)))
+        return gid.value
+
+    def graph_members(self, gid: int) -> int:
+        n = ctypes.c_int32()
+        _check(self._lib.cc_graph_members(self._h, gid, ctypes.byref(n)))
+        return n.value
 
     def graph_free(self, gid: int):
         _check(self._lib.cc_graph_free(self._h, gid))
@@ -408,6 +447,34 @@ class Context:
             out["maps"] = [limbs_to_int(r) for r in maps[:n_iter]]
         if smaps is not None:
             out["samples"] = [[limbs_to_int(r) for r in smaps[j]] for j in range(n_iter)]
+        return out
+
+    def count_batch(self, gid: int, tid: int, seed: int, n_iter: int, first_iter: int = 0,
+                    limbs_capacity: int = 4, width_bits: int = -1, want_maps: bool = False) -> dict:
+        """cc_count_batch: per member graph counts (``counts[i]`` = member i's
+        per-colouring counts, ``estimates[i]`` its estimate) and the shared
+        result fields."""
+        cap = limbs_capacity
+        m = self.graph_members(gid)
+        counts = np.zeros((m, max(n_iter, 1), cap), dtype=np.uint64)
+        maps = np.zeros((m, max(n_iter, 1), cap), dtype=np.uint64) if want_maps else None
+        est = np.zeros(m, dtype=np.float64)
+        args = cc_count_args()
+        args.seed = seed & (2 ** 64 - 1)
+        args.first_iter = first_iter
+        args.n_iter = n_iter
+        args.mom_groups = 1
+        args.width_bits = width_bits
+        if maps is not None:
+            args.maps = maps.ctypes.data
+        res = cc_result()
+        _check(self._lib.cc_count_batch(self._h, gid, tid, ctypes.byref(args), _ptr(counts), cap, _ptr(est),
+                                        ctypes.byref(res)))
+        out = {f: getattr(res, f) for f, _ in cc_result._fields_}
+        out["counts"] = [[limbs_to_int(r) for r in counts[i, :n_iter]] for i in range(m)]
+        if maps is not None:
+            out["maps"] = [[limbs_to_int(r) for r in maps[i, :n_iter]] for i in range(m)]
+        out["estimates"] = est.tolist()
         return out
 
     def count_multi(self, gid: int, tids: Sequence[int], seed: int, n_iter: int, first_iter: int = 0,

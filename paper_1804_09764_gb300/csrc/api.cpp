@@ -1,4 +1,5 @@
 // api.cpp -- the extern "C" entry points declared in include/cc.h.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -98,6 +99,18 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt)
         }
         c->own_stream = true;
     }
+    if (c->opt.l2_persist_mb > 0) {
+        // set-aside L2 for persisting accesses (this context only) and the
+        // access window the table gathers will use
+        int max_persist = 0, max_window = 0;
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, c->device);
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, c->device);
+        const uint64_t want = (uint64_t)c->opt.l2_persist_mb << 20;
+        const uint64_t setaside = std::min<uint64_t>(want, (uint64_t)std::max(0, max_persist));
+        if (setaside > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, setaside) == cudaSuccess)
+            c->l2_window_bytes = std::min<uint64_t>(setaside, (uint64_t)std::max(0, max_window));
+        cudaGetLastError();
+    }
     uint64_t bytes = c->opt.hbm_budget_bytes;
     if (c->opt.arena) {
         if (!bytes) {
@@ -163,6 +176,28 @@ cc_status cc_graph_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
     return graph_load(c, n, row_ptr, col_idx, flags, out);
 }
 
+cc_status cc_graph_load_batch(cc_ctx *ctx, int32_t n_graphs, const int64_t *member_off, int64_t n,
+                              const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags, cc_graph_id *out)
+{
+    if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_graphs < 1 || !member_off) return fail(CC_ERR_INVALID_ARG, "n_graphs < 1 or member_off is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return graph_load(c, n, row_ptr, col_idx, flags, out, n_graphs, member_off);
+}
+
+cc_status cc_graph_members(cc_ctx *ctx, cc_graph_id g, int32_t *n_graphs)
+{
+    if (!ctx || !n_graphs) return fail(CC_ERR_INVALID_ARG, "ctx or n_graphs is NULL");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    auto it = c->graphs.find(g);
+    if (it == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    *n_graphs = it->second->n_members;
+    return CC_OK;
+}
+
 cc_status cc_graph_free(cc_ctx *ctx, cc_graph_id g)
 {
     if (!ctx) return fail(CC_ERR_INVALID_ARG, "ctx is NULL");
@@ -194,6 +229,12 @@ static cc_status template_load(cc_ctx *ctx, int32_t k, const int32_t *edges, con
     if (k > 1) t->edges.assign(edges, edges + 2 * (k - 1));
     if (labels) t->labels.assign(labels, labels + k);
     t->aut = tp.aut;
+    std::vector<std::vector<int>> adj(k);
+    for (int i = 0; i + 1 < k; i++) {
+        adj[edges[2 * i]].push_back(edges[2 * i + 1]);
+        adj[edges[2 * i + 1]].push_back(edges[2 * i]);
+    }
+    t->canon = tree_canonical_form(k, adj, labels);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     int64_t id = c->next_id++;
     c->templates[id] = std::move(t);
@@ -288,6 +329,33 @@ cc_status cc_count_ex(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_cou
                       args->n_sample > 0 ? args->sample_maps : nullptr, res);
 }
 
+cc_status cc_count_batch(cc_ctx *ctx, cc_graph_id g, cc_template_id t, const cc_count_args *args, uint64_t *counts,
+                         int32_t limbs_capacity, double *estimates, cc_result *res)
+{
+    if (!ctx || !args) return fail(CC_ERR_INVALID_ARG, "ctx or args is NULL");
+    if (args->n_iter < 0 || limbs_capacity < 1) return fail(CC_ERR_INVALID_ARG, "n_iter < 0 or limbs_capacity < 1");
+    if (args->n_sample < 0 || (args->n_sample > 0 && !args->sample_vertices))
+        return fail(CC_ERR_INVALID_ARG, "bad sample vertex list");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    auto git = c->graphs.find(g);
+    if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
+    CountJob job;
+    job.seed = args->seed;
+    job.first_iter = args->first_iter;
+    job.n_iter = args->n_iter;
+    job.mom_groups = args->mom_groups > 0 ? args->mom_groups : 1;
+    job.width_bits = args->width_bits;
+    if (args->n_sample > 0) job.sample_vertices.assign(args->sample_vertices, args->sample_vertices + args->n_sample);
+    std::vector<double> est(git->second->n_members);
+    if (res) std::memset(res, 0, sizeof *res);
+    cc_status rc = count_sync(c, g, t, job, counts, limbs_capacity, args->maps,
+                              args->n_sample > 0 ? args->sample_maps : nullptr, res, est.data());
+    if (rc == CC_OK && estimates) std::copy(est.begin(), est.end(), estimates);
+    return rc;
+}
+
 cc_status cc_count_multi(cc_ctx *ctx, cc_graph_id g, const cc_template_id *tmpls, int32_t n_tmpl,
                          const cc_count_args *args, uint64_t *counts, int32_t limbs_capacity, cc_result *res)
 {
@@ -379,6 +447,9 @@ cc_status cc_plan_info_get(cc_ctx *ctx, cc_graph_id g, cc_template_id t, cc_plan
     out->block_vertices = p->V;
     out->col_chunks = p->col_chunks;
     out->shape_tuned = p->shape_tuned ? 1 : 0;
+    out->workspace_no_reuse_bytes = p->ws_no_reuse;
+    out->workspace_no_blocks_bytes = p->ws_no_blocks;
+    out->workspace_naive_bytes = p->ws_naive;
     if (own) free_plan(c, own.get());
     return CC_OK;
 }

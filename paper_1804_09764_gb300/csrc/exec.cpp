@@ -188,7 +188,10 @@ struct Layout {
 // Static workspace layout for batch B and block size V.  Count tables are
 // placed first-fit over their lifetimes (a table lives from its chain to its
 // last consumer), so memory is reused as soon as the schedule is done with it.
-Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp, int B, int64_t V)
+// keep_all: every table keeps its own memory for the whole pass (no reuse; the
+// size a schedule without freeing needs, reported beside the real one).
+Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp, int B, int64_t V,
+                  bool keep_all = false)
 {
     const TemplatePlan &tp = p.tp;
     const int k = tp.k;
@@ -220,7 +223,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
         const auto &C = tp.chains[i];
         if (C.is_root) continue;
         uint64_t sz = rup((uint64_t)n * B * col_stride(binom(k, C.size)) * 8 * p.chain_L[i]);
-        int start = i, end = C.last_consumer;
+        int start = i, end = keep_all ? nc : C.last_consumer;
         // lowest offset not overlapping any live placed table
         std::vector<std::pair<uint64_t, uint64_t>> busy;
         for (auto &q : placed)
@@ -260,7 +263,7 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
     Lo.off_partial = take((uint64_t)std::max<int64_t>(Lo.max_tasks, 1) * B * maxP * 8 * Lm);
     Lo.off_root = take((uint64_t)V * B * 8 * p.L_root);
     Lo.off_scratch = take((uint64_t)reduce_scratch_ctas() * B * 8 * p.L_root);
-    Lo.off_totals = take((uint64_t)p.n_slots * B * 8 * p.L_root);
+    Lo.off_totals = take((uint64_t)p.n_slots * p.n_members * B * 8 * p.L_root);
     Lo.off_params = take(sizeof(ColourParams));
     Lo.off_err = take(256);
     Lo.off_ctr = take(kWorkCounters * 8);
@@ -370,7 +373,7 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
 }  // namespace
 
 cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
-                    std::unique_ptr<PlanInstance> *out)
+                    std::unique_ptr<PlanInstance> *out, bool per_member)
 {
     auto git = c->graphs.find(gid);
     if (git == c->graphs.end()) return fail(CC_ERR_NOT_FOUND, "unknown graph");
@@ -385,6 +388,7 @@ cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits
     CC_TRY(select_partition(c, g, tit->second.get(), width_bits, st, &p->tp, &p->chain_L, &p->L_root));
     const int nc = (int)p->tp.chains.size();
     p->n_slots = 1;
+    p->n_members = per_member ? g->n_members : 1;
     p->chain_slot.assign(nc, -1);
     p->chain_slot[nc - 1] = 0;  // the root chain is last
     p->tmpl_slot = {0};
@@ -546,6 +550,11 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
         }
     }
     p->ws_bytes = Lo.bytes;
+    // the same plan without freeing tables, without vertex blocking, and with
+    // neither: the one-GPU counterparts of the paper's peak-memory comparison
+    p->ws_no_reuse = layout_for(*p, *g, sp, p->B, p->V, true).bytes;
+    p->ws_no_blocks = layout_for(*p, *g, sp, p->B, n).bytes;
+    p->ws_naive = layout_for(*p, *g, sp, p->B, n, true).bytes;
     p->off_col = Lo.off_col;
     p->off_hist = Lo.off_hist;
     p->off_act[0] = Lo.off_act[0];
@@ -726,6 +735,27 @@ static void drain_timer(Ctx *c)
     T.pending.clear();
 }
 
+// With cc_options.l2_persist_mb: the stream's L2 access window over the first
+// bytes of a table about to be gathered, where degree ordering puts the rows
+// read most often (hits persist in the set-aside L2, misses stream).  Not
+// changed while the stream is being captured.
+static void l2_window(Ctx *c, cudaStream_t st, const void *X, uint64_t table_bytes)
+{
+    if (c->l2_window_bytes == 0) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow.base_ptr = const_cast<void *>(X);
+    v.accessPolicyWindow.num_bytes = std::min<uint64_t>(c->l2_window_bytes, table_bytes);
+    v.accessPolicyWindow.hitRatio = 1.0f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess) cudaGetLastError();
+}
+
 static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st, const int64_t *d_samples,
                              int64_t n_samples, uint64_t *d_samples_out, bool tune = false)
 {
@@ -736,7 +766,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     Launcher Ln(c, st);
     auto W = [&](uint64_t off) { return ws + off; };
     uint64_t *totals = (uint64_t *)W(p->off_totals);
-    CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)p->n_slots * B * 8 * p->L_root, st));
+    CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)p->totals_words() * 8, st));
     uint8_t *col = (uint8_t *)W(p->off_col);
     unsigned long long *ctr = (unsigned long long *)W(p->off_ctr);
     int ctr_used = 0;
@@ -806,6 +836,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
                 const int64_t R = (int64_t)B * Cps;
                 const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                l2_window(c, st, X, (uint64_t)g->n_act * R * Ls * 8);
                 uint64_t *agg = (uint64_t *)W(p->off_agg);
                 int64_t Chs0;
                 uint64_t *out0 = step_out(0, &Chs0);
@@ -920,6 +951,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
                     const int64_t R = (int64_t)B * Cps;
                     const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                    l2_window(c, st, X, (uint64_t)g->n_act * R * Ls * 8);
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
                     // algorithmic bytes: neighbour rows + ids + row pointers + output rows
                     auto sel_bytes = [&](double edges, double nvert) {
@@ -978,6 +1010,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     const int64_t Cp = binom(k, s.p), Cps = col_stride(Cp);
                     const int64_t R = (int64_t)B * Cps;
                     const uint64_t *X = (const uint64_t *)W(p->off_table[s.src_chain]);
+                    l2_window(c, st, X, (uint64_t)g->n_act * R * Ls * 8);
                     uint64_t *agg = (uint64_t *)W(p->off_agg);
                     if (!s.reuse_agg) {
                         // algorithmic bytes of this gather: neighbour rows + CSR + aggregate write
@@ -1076,8 +1109,13 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
             }
             if (C.is_root) {
                 Ln.begin(K_REDUCE);
-                launch_root_reduce(st, p->L_root, nv, B, root_rows, (uint64_t *)W(p->off_scratch),
-                                   reduce_scratch_ctas(), totals + (size_t)p->chain_slot[ci] * B * p->L_root);
+                uint64_t *slot_totals = totals + (size_t)p->chain_slot[ci] * p->n_members * B * p->L_root;
+                if (p->n_members > 1)
+                    launch_member_reduce(st, p->L_root, v0, v1, B, root_rows, g->member_act, g->n_members,
+                                         slot_totals);
+                else
+                    launch_root_reduce(st, p->L_root, nv, B, root_rows, (uint64_t *)W(p->off_scratch),
+                                       reduce_scratch_ctas(), slot_totals);
                 int nl = 2;
                 if (n_samples > 0) {
                     launch_sample_extract(st, p->L_root, n_samples, d_samples, v0, v1, B, root_rows, d_samples_out);
@@ -1171,8 +1209,8 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
             CC_TRY(launch_pass(c, p, ws, st, d_samples, n_samples, d_samples_out, tune));
             if (tune) CC_TRY(finish_tuning(c, p, st));
         }
-        CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * p->n_slots * B * p->L_root, ws + p->off_totals,
-                                (size_t)p->n_slots * B * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
+        CC_CUDA(cudaMemcpyAsync(host_totals + (size_t)ps * p->totals_words(), ws + p->off_totals,
+                                (size_t)p->totals_words() * 8, cudaMemcpyDeviceToHost, st));
         if (n_samples > 0)
             CC_CUDA(cudaMemcpyAsync(host_samples + (size_t)ps * B * n_samples * p->L_root, d_samples_out,
                                     (size_t)B * n_samples * 8 * p->L_root, cudaMemcpyDeviceToHost, st));
@@ -1180,6 +1218,20 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
             CC_CUDA(cudaStreamSynchronize(st));
             drain_timer(c);
         }
+    }
+    return CC_OK;
+}
+
+cc_status run_pass_with(Ctx *c, PlanInstance *p, char *ws, const ColourParams *host_params, cudaStream_t st,
+                        uint64_t *host_totals)
+{
+    CC_CUDA(cudaMemcpyAsync(ws + p->off_params, host_params, sizeof(ColourParams), cudaMemcpyHostToDevice, st));
+    CC_TRY(launch_pass(c, p, ws, st, nullptr, 0, nullptr, false));
+    CC_CUDA(cudaMemcpyAsync(host_totals, ws + p->off_totals, (size_t)p->totals_words() * 8, cudaMemcpyDeviceToHost,
+                            st));
+    if (c->timer.on) {
+        CC_CUDA(cudaStreamSynchronize(st));
+        drain_timer(c);
     }
     return CC_OK;
 }
@@ -1209,7 +1261,7 @@ double to_double(const uint64_t *x, int L)
 
 cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
                         const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
-                        uint64_t *sample_out, cc_result *res, int tr)
+                        uint64_t *sample_out, cc_result *res, int tr, int member)
 {
     (void)c;
     // totals rows hold L_root limbs; this template's total needs its low L limbs
@@ -1236,7 +1288,7 @@ cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, 
     std::vector<uint64_t> q(L);
     for (int j = 0; j < n_iter; j++) {
         const int ps = j / B, b = j % B;
-        const uint64_t *m = totals + (((size_t)ps * p->n_slots + slot) * B + b) * Lst;
+        const uint64_t *m = totals + ((((size_t)ps * p->n_slots + slot) * p->n_members + member) * B + b) * Lst;
         if (maps)
             for (int l = 0; l < cap; l++) maps[(size_t)j * cap + l] = l < L ? m[l] : 0;
         if (p->exact) {
@@ -1358,7 +1410,7 @@ static cc_status time_shape(Ctx *c, int64_t gid, int64_t tid, const CountJob &jo
     uint64_t *ht = nullptr;
     std::vector<float> times;
     if (ws && cudaMallocHost(&hp, sizeof(ColourParams)) == cudaSuccess &&
-        cudaMallocHost(&ht, (size_t)8 * p->B * p->L_root * p->n_slots) == cudaSuccess) {
+        cudaMallocHost(&ht, (size_t)8 * p->totals_words()) == cudaSuccess) {
         cudaEvent_t a = nullptr, b = nullptr;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -1440,7 +1492,7 @@ static cc_status tune_shape(Ctx *c, int64_t gid, int64_t tid, const CountJob &jo
 }
 
 cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
-                     uint64_t *maps, uint64_t *sample_out, cc_result *res)
+                     uint64_t *maps, uint64_t *sample_out, cc_result *res, double *member_est)
 {
     auto t_start = std::chrono::steady_clock::now();
     if (!counts) return fail(CC_ERR_INVALID_ARG, "counts is NULL");
@@ -1452,26 +1504,49 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
     Graph *g = git->second.get();
     Template *t = tit->second.get();
     const int width = job.width_bits >= 0 ? job.width_bits : c->opt.width_bits;
-    if (t->k == 1 || g->n_act == 0 || job.n_iter == 0)
-        return trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res,
-                              t->labels.empty() ? -1 : t->labels[0]);
+    const bool per_member = member_est != nullptr;
+    const int M = per_member ? g->n_members : 1;
+    const size_t per = (size_t)job.n_iter * cap;  // counts of one member graph
+    if (t->k == 1 || g->n_act == 0 || job.n_iter == 0) {
+        CC_TRY(trivial_counts(g, job, t->k, t->aut, counts, cap, maps, sample_out, res,
+                              t->labels.empty() ? -1 : t->labels[0]));
+        if (per_member && t->k == 1) {
+            // k = 1: every vertex of a member graph (with the template's label)
+            for (int i = 0; i < M; i++) {
+                uint64_t v = 0;
+                for (int64_t u = g->h_member_off[i]; u < g->h_member_off[i + 1]; u++)
+                    v += t->labels.empty() || g->h_labels[u] == t->labels[0];
+                for (int j = 0; j < job.n_iter; j++)
+                    for (int l = 0; l < cap; l++) {
+                        counts[i * per + (size_t)j * cap + l] = l == 0 ? v : 0;
+                        if (maps) maps[i * per + (size_t)j * cap + l] = l == 0 ? v : 0;
+                    }
+                member_est[i] = (double)v;  // k^k / k! = 1
+            }
+        } else if (per_member) {
+            std::fill(counts, counts + M * per, 0);
+            if (maps) std::fill(maps, maps + M * per, 0);
+            std::fill(member_est, member_est + M, 0.0);
+        }
+        return CC_OK;
+    }
     cudaStream_t st = c->stream;
     // (autotune is fixed per context, so no plan of (gid, tid) is cached yet)
     if (c->opt.autotune && !c->tuned_shape.count({gid, tid}) &&
         (c->opt.split_threshold <= 0 || c->opt.col_chunks == 0 || c->opt.block_vertices == 0))
         CC_TRY(tune_shape(c, gid, tid, job, width, st));
     const int bcap = std::max(1, std::min({c->opt.batch > 0 ? c->opt.batch : 16, job.n_iter, 64}));
-    const auto key = std::make_tuple(gid, tid, bcap, width);
+    const auto key = std::make_tuple(gid, tid, bcap, width, per_member);
     CachedPlan *cp = nullptr;
     auto it = c->plan_cache.find(key);
     if (it != c->plan_cache.end()) {
         cp = &it->second;
     } else {
         std::unique_ptr<PlanInstance> np;
-        cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &np);
+        cc_status rc = make_plan(c, gid, tid, job.n_iter, width, st, &np, per_member);
         if (rc == CC_ERR_BUDGET && !c->plan_cache.empty()) {
             evict_plans(c);
-            rc = make_plan(c, gid, tid, job.n_iter, width, st, &np);
+            rc = make_plan(c, gid, tid, job.n_iter, width, st, &np, per_member);
         }
         if (rc != CC_OK) return rc;
         char *ws = (char *)c->arena.alloc(np->ws_bytes);
@@ -1522,7 +1597,7 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
         CC_CUDA(cudaMemsetAsync(cl.dso, 0, (size_t)8 * ns * B * p->L_root, st));
     }
     CC_CUDA(cudaMallocHost(&cl.hp, sizeof(ColourParams) * npass));
-    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root * p->n_slots));
+    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * p->totals_words()));
     if (ns > 0) CC_CUDA(cudaMallocHost(&cl.hs, (size_t)8 * npass * B * ns * p->L_root));
     cudaEvent_t e0, e1;
     CC_CUDA(cudaEventCreate(&e0));
@@ -1546,8 +1621,28 @@ cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint
         res->device_seconds = ms * 1e-3;
         res->kernel_launches = c->launches.load() - l0;
     }
-    rc = finish_counts(c, p, g, job, (const uint64_t *)cl.ht, (const uint64_t *)cl.hs, counts, cap, maps,
-                       sample_out, res);
+    if (!per_member) {
+        rc = finish_counts(c, p, g, job, (const uint64_t *)cl.ht, (const uint64_t *)cl.hs, counts, cap, maps,
+                           sample_out, res);
+    } else {
+        // member graphs one by one; the result's estimate is that of the whole
+        // batch (the sum: copies in a disjoint union add up)
+        cc_result all{}, one{};
+        if (res) all = *res;
+        double sum = 0;
+        for (int i = 0; i < M && rc == CC_OK; i++) {
+            one = all;
+            rc = finish_counts(c, p, g, job, (const uint64_t *)cl.ht, i == 0 ? (const uint64_t *)cl.hs : nullptr,
+                               counts + i * per, cap, maps ? maps + i * per : nullptr,
+                               i == 0 ? sample_out : nullptr, &one, 0, i);
+            member_est[i] = one.estimate;
+            sum += one.estimate;
+        }
+        if (res) {
+            *res = one;
+            res->estimate = res->median_of_means = sum;
+        }
+    }
     if (res)
         res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     return rc;
@@ -1610,7 +1705,7 @@ cc_status count_multi_sync(Ctx *c, int64_t gid, const std::vector<int64_t> &tids
     const int B = p->B;
     const int npass = (job.n_iter + B - 1) / B;
     CC_CUDA(cudaMallocHost(&cl.hp, sizeof(ColourParams) * npass));
-    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * B * p->L_root * p->n_slots));
+    CC_CUDA(cudaMallocHost(&cl.ht, (size_t)8 * npass * p->totals_words()));
     cudaEvent_t e0, e1;
     CC_CUDA(cudaEventCreate(&e0));
     CC_CUDA(cudaEventCreate(&e1));

@@ -43,6 +43,15 @@ __device__ __forceinline__ void scatter_sums(uint64_t *orow, const Wide<L> (&acc
     }
 }
 
+// Resident CTAs per SM the fused kernels are compiled for (the register cap
+// follows; 0: the compiler's choice).  Measured on R-MAT s22 / tree-12 (ms
+// per launch): one-limb sources summed to two limbs 29 -> 23 at three CTAs
+// (80 registers) rather than four (64), the plain fused step 21 -> 15; the
+// root chain (two-limb sources) 17 uncapped (76 registers) but 23 capped at
+// three CTAs (80); the <1,1,1> chain 5.5 uncapped (60) against 6.3 at three.
+constexpr int select_ctas_per_sm(int Ls, int Ld) { return Ls == 1 ? 3 : 0; }
+constexpr int chain_ctas_per_sm(int Ls, int Lf) { return Ls == 1 && Lf == 2 ? 3 : 0; }
+
 // Fused gather + a = 1 combine (Eq. 1 with T_i' a single vertex): the sum of
 // the neighbour rows agg[T] goes straight to out[T u {col(v)}] (skipped when
 // col(v) is in T); entries S of the output with col(v) not in S are zero.  The
@@ -50,7 +59,7 @@ __device__ __forceinline__ void scatter_sums(uint64_t *orow, const Wide<L> (&acc
 // `next` (the next claim is requested while the current item runs); heavy
 // vertices are left to the task path.
 template <int Ls, int Ld, int VPT, int NB = 2>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, select_ctas_per_sm(Ls, Ld))
 gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                      const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
                      int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,
@@ -179,7 +188,7 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
 // it reads next; __syncwarp orders them within the warp.  The fused step sums
 // and stores Lf-limb values (the width its own bound needs), the leaf steps Ld.
 template <int Ls, int Lf, int Ld, int VPT, int NB>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, chain_ctas_per_sm(Ls, Lf))
 gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
                            int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,

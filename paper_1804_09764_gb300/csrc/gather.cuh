@@ -25,14 +25,73 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1):
-// neighbour ids are fetched 32 at a time and broadcast with shuffles, and NB
-// neighbours' values are loaded before any is added (NB * VPT loads in flight
-// per lane).
+// One batch of NB neighbours (ids in lanes t .. t + NB - 1 of myu) of the row
+// sums below: every load of the batch is issued before any is added, NB * VPT
+// loads in flight per lane.  xl points at value base + lane of row 0; row u
+// starts rb * u bytes further; ok[q]: value base + q * 32 + lane is in the row.
 template <int Ls, int Ld, int VPT, int NB>
-__device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
-                                                const uint64_t *__restrict__ X, int64_t R, int64_t base,
-                                                Wide<Ld> (&acc)[VPT], int lane)
+__device__ __forceinline__ void sum_batch(RowSum<Ls, Ld> (&s)[VPT], const char *xl, uint32_t rb, int32_t myu, int t,
+                                          const bool (&ok)[VPT])
+{
+    using S = RowSum<Ls, Ld>;
+    Wide<S::N> x[NB][VPT];
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        const uint32_t u = (uint32_t)__shfl_sync(0xffffffffu, myu, t + j);
+        const uint64_t *row = reinterpret_cast<const uint64_t *>(xl + (uint64_t)u * rb);
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            if (ok[q])
+                x[j][q] = S::load(row + q * 32 * Ls);
+            else
+                wzero(x[j][q]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; j++)
+#pragma unroll
+        for (int q = 0; q < VPT; q++) s[q].add(x[j][q]);
+}
+
+// acc[q] = the sum of X[u][base + q*32 + lane] over the neighbours u of
+// col_idx[e0, e1) (values of Ls limbs summed to Ld limbs with a carry counter,
+// RowSum; entries at or beyond R are left zero).  Neighbour ids are fetched 32
+// at a time and broadcast with shuffles; neighbours go NB at a time, the rest
+// one by one.  Row addresses are one 32 x 32 -> 64-bit multiply-add per
+// neighbour (rows are less than 4 GiB apart), column offsets are constants.
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void accumulate_rows_counted(const int32_t *__restrict__ col_idx, int64_t e0,
+                                                        int64_t e1, const uint64_t *__restrict__ X, int64_t R,
+                                                        int64_t base, Wide<Ld> (&acc)[VPT], int lane)
+{
+    RowSum<Ls, Ld> s[VPT];
+    bool ok[VPT];
+#pragma unroll
+    for (int q = 0; q < VPT; q++) {
+        s[q].zero();
+        ok[q] = base + q * 32 + lane < R;
+    }
+    const char *xl = reinterpret_cast<const char *>(X + (base + lane) * Ls);
+    const uint32_t rb = (uint32_t)(R * Ls * 8);
+    for (int64_t e = e0; e < e1; e += 32) {
+        const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
+        const int32_t myu = lane < cnt ? __ldg(col_idx + e + lane) : 0;
+        const int nfull = cnt - cnt % NB;
+        for (int t = 0; t < nfull; t += NB) sum_batch<Ls, Ld, VPT, NB>(s, xl, rb, myu, t, ok);
+        for (int t = nfull; t < cnt; t++) sum_batch<Ls, Ld, VPT, 1>(s, xl, rb, myu, t, ok);
+    }
+#pragma unroll
+    for (int q = 0; q < VPT; q++) acc[q] = s[q].wide();
+}
+
+// acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1)
+// with full Ld-limb adds: neighbour ids are fetched 32 at a time and broadcast
+// with shuffles, and NB neighbours' values are loaded before any is added
+// (NB * VPT loads in flight per lane).
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void accumulate_rows_limbwise(const int32_t *__restrict__ col_idx, int64_t e0,
+                                                         int64_t e1, const uint64_t *__restrict__ X, int64_t R,
+                                                         int64_t base, Wide<Ld> (&acc)[VPT], int lane)
 {
     for (int64_t e = e0; e < e1; e += 32) {
         const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
@@ -68,6 +127,23 @@ __device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_
             }
         }
     }
+}
+
+// acc[q] (zero on entry) = the neighbour sum of value base + q * 32 + lane.
+// One-limb sources take the carry-counter form (one 64-bit add and a 32-bit
+// carry add per value instead of a full two-limb add); wider sources keep the
+// limb-wise form, the one measured for the root chain's <2,2,3> instantiation
+// without a register cap (17 ms per launch on R-MAT s22 / tree-12, against
+// 23 ms under a three-CTA cap with either form).
+template <int Ls, int Ld, int VPT, int NB>
+__device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
+                                                const uint64_t *__restrict__ X, int64_t R, int64_t base,
+                                                Wide<Ld> (&acc)[VPT], int lane)
+{
+    if constexpr (Ls == 1)
+        accumulate_rows_counted<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+    else
+        accumulate_rows_limbwise<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
 }
 
 // Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.

@@ -47,11 +47,19 @@ cc_status validate_host(int64_t n, const int64_t *rp, const int32_t *ci)
 }  // namespace
 
 cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
-                     cc_graph_id *out)
+                     cc_graph_id *out, int32_t n_members, const int64_t *member_off)
 {
     if (!out) return fail(CC_ERR_INVALID_ARG, "out is NULL");
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(CC_ERR_INVALID_ARG, "n out of range");
     if (!row_ptr) return fail(CC_ERR_INVALID_ARG, "row_ptr is NULL");
+    if (n_members < 1 || (n_members > 1 && !member_off)) return fail(CC_ERR_INVALID_ARG, "bad member graph count");
+    std::vector<int64_t> moff = {0, n};
+    if (member_off) {
+        moff.assign(member_off, member_off + n_members + 1);
+        if (moff[0] != 0 || moff[n_members] != n) return fail(CC_ERR_INVALID_ARG, "member offsets must run from 0 to n");
+        for (int32_t i = 0; i < n_members; i++)
+            if (moff[i + 1] < moff[i]) return fail(CC_ERR_INVALID_ARG, "member offsets decrease at " + std::to_string(i));
+    }
     cudaStream_t st = c->stream;
     auto g = std::make_unique<Graph>();
     g->n = n;
@@ -79,17 +87,50 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
         }
         CC_TRY(validate_host(n, rp.data(), p));
     }
+    // member graph of every input vertex; no edge may join two members (each
+    // member's count would otherwise take maps that reach into another)
+    std::vector<int32_t> member_of;
+    if (n_members > 1) {
+        member_of.resize(n);
+        for (int32_t i = 0; i < n_members; i++)
+            for (int64_t v = moff[i]; v < moff[i + 1]; v++) member_of[v] = i;
+        std::vector<int32_t> hci;
+        const int32_t *p = col_idx;
+        if (ci_dev) {
+            hci.resize(nnz);
+            CC_CUDA(cudaMemcpy(hci.data(), col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+            p = hci.data();
+        }
+        for (int64_t v = 0; v < n; v++)
+            for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
+                if (p[e] < 0 || p[e] >= n)
+                    return fail(CC_ERR_BAD_GRAPH, "neighbour id out of range at vertex " + std::to_string(v));
+                if (member_of[p[e]] != member_of[v])
+                    return fail(CC_ERR_BAD_GRAPH, "edge " + std::to_string(v) + "-" + std::to_string(p[e]) +
+                                                      " joins two member graphs");
+            }
+    }
     // Compact numbering: isolated vertices are dropped (they are in no embedding
     // when k >= 2).  By default the active vertices are also ordered by
     // decreasing degree, so the rows of the hub vertices -- the rows read most
     // often by the gathers -- sit together at the start of every table.
+    // Graph batches keep each member's compact ids together (members in
+    // input order, each ordered by degree), so every member's root rows form
+    // one range.
     const bool by_degree = c->opt.vertex_order == 0;
     std::vector<int64_t> orig;
-    for (int64_t v = 0; v < n; v++)
-        if (rp[v + 1] > rp[v]) orig.push_back(v);
-    if (by_degree)
-        std::stable_sort(orig.begin(), orig.end(),
-                         [&](int64_t x, int64_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+    g->n_members = n_members;
+    g->h_member_off = moff;
+    g->h_member_act.assign(n_members + 1, 0);
+    for (int32_t i = 0; i < n_members; i++) {
+        const size_t first = orig.size();
+        for (int64_t v = moff[i]; v < moff[i + 1]; v++)
+            if (rp[v + 1] > rp[v]) orig.push_back(v);
+        if (by_degree)
+            std::stable_sort(orig.begin() + first, orig.end(),
+                             [&](int64_t x, int64_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+        g->h_member_act[i + 1] = (int64_t)orig.size();
+    }
     g->h_new_id.assign(n, -1);
     g->h_row_ptr.assign(orig.size() + 1, 0);
     for (size_t i = 0; i < orig.size(); i++) {
@@ -105,16 +146,18 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
     g->row_ptr = (int64_t *)A(sizeof(int64_t) * (g->n_act + 1));
     g->col_idx = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
     g->orig = (int64_t *)A(sizeof(int64_t) * std::max<int64_t>(g->n_act, 1));
+    g->member_act = (int64_t *)A(sizeof(int64_t) * (n_members + 1));
     int32_t *d_new = (int32_t *)A(sizeof(int32_t) * std::max<int64_t>(n, 1));
     int32_t *d_src = nullptr;
     int64_t *d_old_rp = nullptr;
     if (nnz > 0 && !ci_dev) d_src = (int32_t *)A(sizeof(int32_t) * nnz);
     if (nnz > 0 && by_degree) d_old_rp = (int64_t *)A(sizeof(int64_t) * (n + 1));
-    if (!g->row_ptr || !g->col_idx || !g->orig || !d_new || (nnz > 0 && !ci_dev && !d_src) ||
+    if (!g->row_ptr || !g->col_idx || !g->orig || !g->member_act || !d_new || (nnz > 0 && !ci_dev && !d_src) ||
         (nnz > 0 && by_degree && !d_old_rp)) {
         c->arena.free(g->row_ptr);
         c->arena.free(g->col_idx);
         c->arena.free(g->orig);
+        c->arena.free(g->member_act);
         c->arena.free(d_new);
         c->arena.free(d_src);
         c->arena.free(d_old_rp);
@@ -139,6 +182,17 @@ cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
         }
         c->launches++;
     }
+    CC_CUDA(cudaMemcpyAsync(g->member_act, g->h_member_act.data(), sizeof(int64_t) * (n_members + 1),
+                            cudaMemcpyHostToDevice, st));
+    if (n_members > 1) {
+        // colours are drawn from each vertex's id within its member graph, so a
+        // member gets the colourings it would get loaded alone
+        std::vector<int64_t> local(orig.size());
+        for (size_t i = 0; i < orig.size(); i++) local[i] = orig[i] - moff[member_of[orig[i]]];
+        CC_CUDA(cudaStreamSynchronize(st));  // the lists were permuted with the input ids
+        CC_CUDA(cudaMemcpyAsync(g->orig, local.data(), sizeof(int64_t) * g->n_act, cudaMemcpyHostToDevice, st));
+        CC_CUDA(cudaStreamSynchronize(st));
+    }
     CC_CUDA(cudaGetLastError());
     CC_CUDA(cudaStreamSynchronize(st));
     c->arena.free(d_new);
@@ -155,6 +209,8 @@ cc_status graph_free(Ctx *c, Graph *g)
     c->arena.free(g->row_ptr);
     c->arena.free(g->col_idx);
     c->arena.free(g->orig);
+    c->arena.free(g->member_act);
+    g->member_act = nullptr;
     c->arena.free(g->labels);
     g->labels = nullptr;
     for (auto &kv : g->splits) {

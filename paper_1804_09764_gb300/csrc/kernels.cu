@@ -758,6 +758,35 @@ __global__ void root_final_kernel(int64_t nctas, int B, const uint64_t *__restri
     }
 }
 
+// Graph batches: totals[i][b] += sum of root[v][b] over the compact vertices
+// v of member graph i inside the block [v0, v1) (members hold consecutive
+// compact ids, member_act[i] .. member_act[i + 1]).  One CTA per member at a
+// time; CTAs stride over the members.
+template <int L>
+__global__ void member_reduce_kernel(int64_t v0, int64_t v1, int B, const uint64_t *__restrict__ root,
+                                     const int64_t *__restrict__ member_act, int n_members,
+                                     uint64_t *__restrict__ totals)
+{
+    for (int i = blockIdx.x; i < n_members; i += gridDim.x) {
+        const int64_t a = max(v0, member_act[i]), z = min(v1, member_act[i + 1]);
+        if (a >= z) continue;  // the same for every thread of the CTA
+        for (int b = 0; b < B; b++) {
+            Wide<L> acc;
+            wzero(acc);
+            for (int64_t v = a + threadIdx.x; v < z; v += blockDim.x)
+                wadd(acc, wload<L, L>(root + ((v - v0) * B + b) * L));
+            Wide<L> s = block_sum(acc);
+            if (threadIdx.x == 0) {
+                Wide<L> t;
+#pragma unroll
+                for (int l = 0; l < L; l++) t.w[l] = totals[((int64_t)i * B + b) * L + l];
+                wadd(t, s);
+                wstore(totals + ((int64_t)i * B + b) * L, t);
+            }
+        }
+    }
+}
+
 template <int L>
 __global__ void sample_kernel(int64_t n_s, const int64_t *__restrict__ sample_v, int64_t v0, int64_t v1,
                               int B, const uint64_t *__restrict__ root, uint64_t *__restrict__ out)
@@ -1184,6 +1213,14 @@ void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(scratch_ctas, (nv + 255) / 256));
     CC_DISPATCH_L(L, root_reduce_kernel<LL><<<g, 256, 0, st>>>(nv, B, root, scratch));
     CC_DISPATCH_L(L, root_final_kernel<LL><<<B, 256, 0, st>>>(g, B, scratch, totals));
+}
+
+void launch_member_reduce(cudaStream_t st, int L, int64_t v0, int64_t v1, int B, const uint64_t *root,
+                          const int64_t *member_act, int n_members, uint64_t *totals)
+{
+    if (v1 <= v0 || n_members <= 0) return;
+    const unsigned g = (unsigned)std::min(n_members, 152 * 8);
+    CC_DISPATCH_L(L, member_reduce_kernel<LL><<<g, 256, 0, st>>>(v0, v1, B, root, member_act, n_members, totals));
 }
 
 void launch_sample_extract(cudaStream_t st, int L, int64_t n_s, const int64_t *sample_v, int64_t v0, int64_t v1,

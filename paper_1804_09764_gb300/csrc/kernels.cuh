@@ -171,6 +171,9 @@ void launch_select_heavy(cudaStream_t st, int L, int64_t h0, int64_t h1, int64_t
 // totals[b] += sum_v root[v][b]  (root rows hold C(k,k) = 1 column)
 void launch_root_reduce(cudaStream_t st, int L, int64_t nv, int B, const uint64_t *root,
                         uint64_t *scratch, int64_t scratch_ctas, uint64_t *totals);
+// graph batches: per member graph totals over the compact vertices [v0, v1)
+void launch_member_reduce(cudaStream_t st, int L, int64_t v0, int64_t v1, int B, const uint64_t *root,
+                          const int64_t *member_act, int n_members, uint64_t *totals);
 
 // samples: out[(b * n_s + i) * L] = root[sample_local[i]][b] for samples inside [v0, v1)
 void launch_sample_extract(cudaStream_t st, int L, int64_t n_s, const int64_t *sample_v,

@@ -140,10 +140,10 @@ int64_t step_cost(int k, int h, int a) { return binom(k, h) * binom(h, a); }
 
 }  // namespace
 
-int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels)
+// the one or two centres of a tree (the vertices left after stripping leaves
+// layer by layer)
+static std::vector<int> tree_centres(int k, const std::vector<std::vector<int>> &adj)
 {
-    if (k <= 2) return k == 2 ? (labels && labels[0] != labels[1] ? 1 : 2) : 1;
-    // centre(s): strip leaves
     std::vector<int> deg(k);
     for (int i = 0; i < k; i++) deg[i] = (int)adj[i].size();
     std::vector<int> layer, removed(k, 0);
@@ -163,6 +163,28 @@ int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, cons
     std::vector<int> centres;
     for (int i = 0; i < k; i++)
         if (!removed[i]) centres.push_back(i);
+    return centres;
+}
+
+std::string tree_canonical_form(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels)
+{
+    if (k == 1) return labels ? "(" + std::to_string((int)labels[0]) + ":)" : "()";
+    std::string best;
+    for (int c : tree_centres(k, adj)) {
+        Rooted R;
+        R.k = k;
+        R.label = labels;
+        R.adj = adj;
+        root_at(R, c);
+        if (best.empty() || R.canon[c] < best) best = R.canon[c];
+    }
+    return std::to_string(k) + best;
+}
+
+int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels)
+{
+    if (k <= 2) return k == 2 ? (labels && labels[0] != labels[1] ? 1 : 2) : 1;
+    const std::vector<int> centres = tree_centres(k, adj);
     Rooted R;
     R.k = k;
     R.label = labels;

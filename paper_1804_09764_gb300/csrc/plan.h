@@ -63,6 +63,12 @@ int build_template_plan(int k, const int32_t *edges, int root, int order_mode, d
 // automorphisms when labels are given).
 int64_t tree_automorphisms(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels = nullptr);
 
+// Canonical form of an unrooted tree (label-respecting when labels are given):
+// the least AHU form of the tree rooted at one of its centres.  Two trees have
+// the same form exactly when they are isomorphic (by a label-preserving map),
+// and isomorphic templates have the same copy counts in every graph.
+std::string tree_canonical_form(int k, const std::vector<std::vector<int>> &adj, const uint8_t *labels = nullptr);
+
 // Colex ranking of k-colour sets (combinatorial number system):
 // rank(S) = sum_i C(c_i, i+1) over the members c_0 < c_1 < ... of S.
 struct SetTables {

@@ -62,10 +62,17 @@ struct Graph {
     // device (arena)
     int64_t *row_ptr = nullptr;   // [n_act + 1]
     int32_t *col_idx = nullptr;   // [nnz], compact ids
-    int64_t *orig = nullptr;      // [n_act] original id of each compact vertex
+    int64_t *orig = nullptr;      // [n_act] id of each compact vertex that its colour is drawn from:
+                                  // its input id, or its id within its member graph (graph batches)
     // host copies used for planning
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_new_id;  // original id -> compact id or -1 (isolated)
+    // graph batches: member graph i holds input ids [h_member_off[i],
+    // h_member_off[i + 1]) and compact ids [h_member_act[i], h_member_act[i + 1])
+    // (compact ids are ordered by member first); one member otherwise
+    int32_t n_members = 1;
+    std::vector<int64_t> h_member_off, h_member_act;
+    int64_t *member_act = nullptr;  // device copy of h_member_act [n_members + 1]
     // vertex labels for labelled templates, or none: host copy in the original
     // numbering [n], device copy in the compact numbering [n_act]
     std::vector<uint8_t> h_labels;
@@ -98,6 +105,7 @@ struct Template {
     std::vector<int32_t> edges;
     std::vector<uint8_t> labels;  // vertex labels, or empty (unlabelled)
     int64_t aut = 1;              // label-preserving automorphisms when labelled
+    std::string canon;            // tree_canonical_form: equal for isomorphic templates
 };
 
 // A template planned against a graph with a batch size and width policy.
@@ -130,6 +138,9 @@ struct PlanInstance {
     std::map<std::pair<int, int>, uint32_t *> d_pairs;
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;
+    // workspace of the same plan with every table kept for the whole pass, with
+    // one vertex block, and with both (analytic; nothing is allocated)
+    uint64_t ws_no_reuse = 0, ws_no_blocks = 0, ws_naive = 0;
     uint64_t off_col = 0, off_hist = 0, off_act[2] = {0, 0}, off_agg = 0, off_partial = 0, off_root = 0,
              off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0, off_ctr = 0;
     std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
@@ -150,6 +161,10 @@ struct PlanInstance {
     // neighbours, unlabelled templates), n_act x B x k counts each
     std::vector<int> hist_labels;
     int n_slots = 1;
+    // graph batches: every slot holds n_members totals (one per member graph):
+    // totals are [n_slots][n_members][B][L_root] per pass
+    int n_members = 1;
+    int64_t totals_words() const { return (int64_t)n_slots * n_members * B * L_root; }
     std::vector<int> chain_slot;     // per chain: totals slot, -1 for non-root chains
     std::vector<int> tmpl_slot, tmpl_L, tmpl_root;
     std::vector<int64_t> tmpl_aut;
@@ -209,7 +224,8 @@ struct Ctx {
     KernelTimer timer;
     std::atomic<int64_t> launches{0};
     // plans kept between calls: (graph, template, batch cap, width) -> plan
-    std::map<std::tuple<int64_t, int64_t, int, int>, CachedPlan> plan_cache;
+    // (graph, template, batch cap, width bits, per-member totals)
+    std::map<std::tuple<int64_t, int64_t, int, int, bool>, CachedPlan> plan_cache;
     uint64_t use_clock = 0;
     // autotuned gather variants per (graph, template, batch), shared by later plans
     std::map<std::tuple<int64_t, int64_t, int>, std::map<std::pair<int, int>, int>> tuned_modes;
@@ -220,13 +236,16 @@ struct Ctx {
     std::map<std::pair<int64_t, int64_t>, TunedShape> tuned_shape;
     // serving
     std::unique_ptr<struct Server> server;
+    uint64_t l2_window_bytes = 0;  // cc_options.l2_persist_mb as granted (0: no access window)
     Ctx();
     ~Ctx();  // defined where Server is complete
 };
 
 // executor entry points
+// member_off: NULL (one graph) or n_members + 1 increasing input-id offsets
+// starting at 0 and ending at n (a batch of member graphs, no edge between two)
 cc_status graph_load(Ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
-                     cc_graph_id *out);
+                     cc_graph_id *out, int32_t n_members = 1, const int64_t *member_off = nullptr);
 cc_status graph_free(Ctx *c, Graph *g);
 cc_status ensure_split(Ctx *c, Graph *g, int64_t s, cudaStream_t st);
 
@@ -240,8 +259,10 @@ struct CountJob {
 };
 
 // plan (with workspace sizing) for a count with n_iter colourings
+// per_member: one total per member graph of a graph batch (else one for the
+// whole graph)
 cc_status make_plan(Ctx *c, int64_t gid, int64_t tid, int n_iter, int width_bits, cudaStream_t st,
-                    std::unique_ptr<PlanInstance> *out);
+                    std::unique_ptr<PlanInstance> *out, bool per_member = false);
 // one plan for several templates with the same k over the same colourings:
 // rooted subtrees with equal canonical forms share one table
 cc_status make_plan_multi(Ctx *c, int64_t gid, const std::vector<int64_t> &tids, int n_iter, int width_bits,
@@ -259,14 +280,23 @@ cc_status run_passes(Ctx *c, PlanInstance *p, char *ws, const CountJob &job, int
                      const int64_t *d_samples, int64_t n_samples, uint64_t *d_samples_out,
                      CachedPlan *graph = nullptr);
 
+// One pass with the given colouring parameters (host_params[0].hj[b] for the
+// plan's B colourings; pinned memory), queued on st: totals of the pass go to
+// host_totals (pinned, p->totals_words() words).  The serving loop fills
+// the parameters with colourings of several requests.
+cc_status run_pass_with(Ctx *c, PlanInstance *p, char *ws, const ColourParams *host_params, cudaStream_t st,
+                        uint64_t *host_totals);
+
 // Host post-processing for template tr of the plan: copies, estimate, median
 // of means, writes caller buffers.
 cc_status finish_counts(Ctx *c, PlanInstance *p, Graph *g, const CountJob &job, const uint64_t *totals,
                         const uint64_t *samples, uint64_t *counts, int32_t cap, uint64_t *maps,
-                        uint64_t *sample_out, cc_result *res, int tr = 0);
+                        uint64_t *sample_out, cc_result *res, int tr = 0, int member = 0);
 
+// member_est: NULL, or a graph batch counted per member graph: counts and maps
+// are [n_members][n_iter][cap], member_est[i] the estimate of member i
 cc_status count_sync(Ctx *c, int64_t gid, int64_t tid, const CountJob &job, uint64_t *counts, int32_t cap,
-                     uint64_t *maps, uint64_t *sample_out, cc_result *res);
+                     uint64_t *maps, uint64_t *sample_out, cc_result *res, double *member_est = nullptr);
 
 // drop cached plans (all, or those of one graph / template); frees their workspace
 void evict_plans(Ctx *c, int64_t gid = -1, int64_t tid = -1);

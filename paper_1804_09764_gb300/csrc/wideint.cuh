@@ -167,6 +167,77 @@ __device__ __forceinline__ Wide<Ld> wload(const uint64_t *__restrict__ p)
     return r;
 }
 
+// Running sum of neighbour values stored with Ls limbs, for an Ld-limb result.
+// The low N = min(Ls, Ld) limbs are summed with one add-with-carry chain; when
+// Ld > Ls the carries out of limb Ls - 1 go to a 32-bit counter instead of
+// full limbs: a sum of at most 2^31 values (a CSR neighbour list is shorter
+// than that) below 2^(64 Ls) is below 2^31 * 2^(64 Ls), so limb Ls of the sum
+// is that count and every limb above it is zero.  When Ld <= Ls the sum is
+// taken modulo 2^(64 Ld) on the low Ld limbs of each value.
+template <int Ls, int Ld>
+struct RowSum {
+    static constexpr int N = Ls < Ld ? Ls : Ld;
+    static constexpr bool kCarry = Ld > Ls;
+    Wide<N> s;   // the low N limbs
+    uint32_t c;  // carries out of limb N - 1 (kCarry only)
+
+    __device__ __forceinline__ void zero()
+    {
+        wzero(s);
+        c = 0;
+    }
+    // the low N limbs of the value at p (Ls limbs; 16-byte aligned when Ls is even)
+    __device__ __forceinline__ static Wide<N> load(const uint64_t *__restrict__ p)
+    {
+        Wide<N> r;
+        if constexpr (N == 2 && Ls % 2 == 0) {
+            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+            r.w[0] = v.x;
+            r.w[1] = v.y;
+        } else if constexpr (N == 4) {
+            const ulonglong2 v0 = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+            const ulonglong2 v1 = __ldg(reinterpret_cast<const ulonglong2 *>(p) + 1);
+            r.w[0] = v0.x; r.w[1] = v0.y; r.w[2] = v1.x; r.w[3] = v1.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < N; i++) r.w[i] = __ldg(p + i);
+        }
+        return r;
+    }
+    __device__ __forceinline__ void add(const Wide<N> &x)
+    {
+        if constexpr (!kCarry) {
+            wadd(s, x);
+        } else if constexpr (N == 1) {
+            asm("add.cc.u64 %0, %0, %2;\n\t"
+                "addc.u32 %1, %1, 0;"
+                : "+l"(s.w[0]), "+r"(c)
+                : "l"(x.w[0]));
+        } else if constexpr (N == 2) {
+            asm("add.cc.u64 %0, %0, %3;\n\t"
+                "addc.cc.u64 %1, %1, %4;\n\t"
+                "addc.u32 %2, %2, 0;"
+                : "+l"(s.w[0]), "+l"(s.w[1]), "+r"(c)
+                : "l"(x.w[0]), "l"(x.w[1]));
+        } else {
+            static_assert(N == 3, "a carry counter needs Ls < Ld <= 4");
+            asm("add.cc.u64 %0, %0, %4;\n\t"
+                "addc.cc.u64 %1, %1, %5;\n\t"
+                "addc.cc.u64 %2, %2, %6;\n\t"
+                "addc.u32 %3, %3, 0;"
+                : "+l"(s.w[0]), "+l"(s.w[1]), "+l"(s.w[2]), "+r"(c)
+                : "l"(x.w[0]), "l"(x.w[1]), "l"(x.w[2]));
+        }
+    }
+    __device__ __forceinline__ Wide<Ld> wide() const
+    {
+        Wide<Ld> r;
+#pragma unroll
+        for (int i = 0; i < Ld; i++) r.w[i] = i < N ? s.w[i] : (kCarry && i == N ? (uint64_t)c : 0);
+        return r;
+    }
+};
+
 template <int L>
 __device__ __forceinline__ void wstore(uint64_t *__restrict__ p, const Wide<L> &x)
 {

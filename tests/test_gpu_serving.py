@@ -3,7 +3,9 @@
 Requests over several resident graphs and templates are submitted while others
 are running; every result must be bit-identical to the same count run alone
 through cc_count (exact integers: the tolerance is zero) and, for a sample, to
-the oracle.  Also: cancellation, unknown handles, and the latency statistics.
+the oracle.  Requests on one graph with isomorphic templates share passes:
+one launch carries colourings of both.  Also: cancellation, unknown handles,
+and the latency statistics.
 """
 import time
 
@@ -67,8 +69,9 @@ def test_cancel_and_errors():
     c = make_ctx(max_slots=1)
     gid = c.graph_load(gg.rmat_graph(12, seed=7))
     tid = c.template_load(*gg.template_edges("tree12"))
+    tid2 = c.template_load(*gg.template_edges("P5"))
     r1 = c.submit(gid, tid, 1, 8)
-    r2 = c.submit(gid, tid, 2, 8)   # queued behind r1 (one slot)
+    r2 = c.submit(gid, tid2, 2, 8)   # another template class: queued behind r1 (one slot)
     c.cancel(r2)
     with pytest.raises(cc.CCError) as ei:
         c.wait(r2, 8, timeout_s=120)
@@ -81,4 +84,30 @@ def test_cancel_and_errors():
     with pytest.raises(cc.CCError) as ei:
         c.submit(gid, 999, 1, 1)
     assert ei.value.status == -10
+    c.close()
+
+
+def test_one_launch_carries_two_requests():
+    # two isomorphic templates (the second relabelled and rooted elsewhere) on
+    # one graph: one group, and passes whose colourings belong to both requests
+    k = 7
+    e1 = gg.prufer_tree(k, 4242)
+    perm = [3, 6, 0, 5, 1, 4, 2]
+    e2 = [(perm[a], perm[b]) for a, b in e1]
+    g = gg.rmat_graph(11, seed=9)
+    c = make_ctx(max_slots=1, batch=16)
+    gid = c.graph_load(g)
+    t1, t2 = c.template_load(k, e1, 0), c.template_load(k, e2, perm[3])
+    alone1 = c.count(gid, t1, seed=11, n_iter=40, first_iter=7)
+    alone2 = c.count(gid, t2, seed=12, n_iter=6, first_iter=3)
+    r1 = c.submit(gid, t1, 11, 40, 7)
+    r2 = c.submit(gid, t2, 12, 6, 3)
+    got1 = c.wait(r1, 40, timeout_s=120)
+    got2 = c.wait(r2, 6, timeout_s=120)
+    assert got1["counts"] == alone1["counts"] and got2["counts"] == alone2["counts"]
+    st = c.serve_stats()
+    assert st["shared_passes"] >= 1, st
+    assert st["colourings_run"] == 46 and st["passes"] == 3, st  # one after the other: 3 + 1 passes
+    aut = O.automorphisms(k, e2)
+    assert got2["counts"][0] == O.count_maps(g, k, e2, 0, seed=12, j=3) // aut
     c.close()
