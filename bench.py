@@ -401,7 +401,7 @@ def run_serving(args):
     for r in reqs:
         r["U"] = plan_updates_host(graphs[r["g"]], r["k"], r["e"], 0) * r["n_iter"]
     # served at the offered rate
-    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
+    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=0, autotune=0)
     gids = [ctx.graph_load(g) for g in graphs]
     with ClockSampler(0) as clk:
         served_s, st = served(ctx, gids, reqs)
@@ -436,7 +436,7 @@ def run_serving(args):
     # a sustainable load: fewer, sparser requests, served only (the plain forms'
     # service times do not depend on the rate)
     light = make_requests(args.light_requests, args.light_rate, 4048)
-    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=16, autotune=0)
+    ctx = cc.Context(budget_bytes=budget, max_slots=args.serve_slots, batch=0, autotune=0)
     gids = [ctx.graph_load(g) for g in graphs]
     light_s, st_l = served(ctx, gids, light)
     plain(ctx, gids, light, "plain")
@@ -448,7 +448,8 @@ def run_serving(args):
             "steps": 1, "warmup": 0, "ms_per_step": served_s * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64..u256", "data": "synthetic",
             "config": {"workload": "serve", "graphs": [g.name for g in graphs], "requests": args.requests,
-                       "rate_per_s": args.rate, "slots": args.serve_slots, "batch_cap": 16, "k": "5..12",
+                       "rate_per_s": args.rate, "slots": args.serve_slots,
+                       "batch": "up to 16 colourings per pass, fewer when the budget requires", "k": "5..12",
                        "colourings": "1..16", "arrival_span_s": arrivals[-1]},
             "serving": {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
                         "mean_latency_s": st["mean_latency_s"], "completed": st["completed"],

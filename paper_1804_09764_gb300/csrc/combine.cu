@@ -88,8 +88,28 @@ combine_generic_smem_kernel(int64_t rows, int64_t Ch, int64_t Chs, int64_t Cas, 
             Wide<L> acc;
             wzero(acc);
             if (s < Ch) {
-                for (int64_t q = 0; q < npairs; q++) {
-                    const uint32_t pq = __ldg(pairs + q * Ch + s);
+                // split entries G at a time (all G global loads in flight before
+                // the shared-memory operand reads and multiply-adds that need them)
+                constexpr int G = L <= 2 ? 8 : 4;
+                const uint32_t *ps = pairs + s;
+                int64_t q0 = 0;
+                for (; q0 + G <= npairs; q0 += G) {
+                    uint32_t pq[G];
+#pragma unroll
+                    for (int j = 0; j < G; j++) pq[j] = __ldg(ps + (q0 + j) * Ch);
+#pragma unroll
+                    for (int j = 0; j < G; j++) {
+                        Wide<La> x;
+                        Wide<Lb> y;
+#pragma unroll
+                        for (int l = 0; l < La; l++) x.w[l] = sa[(pq[j] & 0xFFFFu) * La + l];
+#pragma unroll
+                        for (int l = 0; l < Lb; l++) y.w[l] = sp[(pq[j] >> 16) * Lb + l];
+                        wmac_mixed<L, La, Lb>(acc, x, y);
+                    }
+                }
+                for (int64_t q = q0; q < npairs; q++) {
+                    const uint32_t pq = __ldg(ps + q * Ch);
                     Wide<La> x;
                     Wide<Lb> y;
 #pragma unroll

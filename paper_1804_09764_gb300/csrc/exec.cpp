@@ -769,8 +769,19 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     CC_CUDA(cudaMemsetAsync(totals, 0, (size_t)p->totals_words() * 8, st));
     uint8_t *col = (uint8_t *)W(p->off_col);
     unsigned long long *ctr = (unsigned long long *)W(p->off_ctr);
+    // Every persistent launch pulls its work items from a zeroed counter of its
+    // own.  A pass with more launches than counters (many small vertex blocks)
+    // clears them all again once they are used up: the clear is ordered on the
+    // stream after every launch that used them.  (A failed clear is reported by
+    // the cudaGetLastError at the end of the pass.)
     int ctr_used = 0;
-    auto next_counter = [&]() -> unsigned long long * { return ctr_used < kWorkCounters ? ctr + ctr_used++ : nullptr; };
+    auto next_counter = [&]() -> unsigned long long * {
+        if (ctr_used == kWorkCounters) {
+            cudaMemsetAsync(ctr, 0, (size_t)kWorkCounters * 8, st);
+            ctr_used = 0;
+        }
+        return ctr + ctr_used++;
+    };
     CC_CUDA(cudaMemsetAsync(ctr, 0, (size_t)kWorkCounters * 8, st));
     Ln.begin(K_COLOUR);
     launch_colour(st, g->n_act, B, k, g->orig, (const ColourParams *)W(p->off_params), col);

@@ -52,6 +52,7 @@ struct Group {
     std::string canon;
     int L_root = 0;
     std::unique_ptr<PlanInstance> plan;  // planned for the batch size of the pass
+    int planned_for = 0;                 // the batch asked for when planning (the plan's B may be smaller)
     char *ws = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
@@ -357,16 +358,31 @@ void fail_members(Ctx *c, Server *s, Group *gr, cc_status rc)
 }
 
 // Start the next pass of group gr: the pending colourings of its requests in
-// arrival order, as many as the (re)planned batch takes.
-void launch_next(Ctx *c, Server *s, Group *gr)
+// arrival order, as many as the (re)planned batch takes.  When the pending
+// colourings call for another batch size the group is re-planned, halving the
+// batch while the workspace does not fit; if not even one colouring fits while
+// other groups hold workspace, the group waits for them to give it back.  Returns whether a pass
+// was started (or the group's requests finished with an error).
+bool launch_next(Ctx *c, Server *s, Group *gr)
 {
     int pending = 0;
     for (Request *r : gr->members) pending += r->job.n_iter - r->next_j;
-    if (pending <= 0) return;
+    if (pending <= 0) return false;
     const int want = std::min(batch_cap(c), pending);
-    if (!gr->plan || gr->plan->B != want) {
-        cc_status rc = plan_group(c, gr, want);
-        if (rc != CC_OK) return fail_members(c, s, gr, rc);
+    if (!gr->plan || (gr->plan->B != want && gr->planned_for != want)) {
+        cc_status rc = CC_ERR_BUDGET;
+        for (int w = want; w >= 1 && rc == CC_ERR_BUDGET; w = w > 1 ? w / 2 : 0) rc = plan_group(c, gr, w);
+        gr->planned_for = want;
+        bool others_hold = false;  // memory that other groups will give back
+        for (auto &x : s->groups) others_hold |= x.get() != gr && x->plan != nullptr;
+        if (rc == CC_ERR_BUDGET && others_hold) {
+            s->st.admissions_deferred++;
+            return false;
+        }
+        if (rc != CC_OK) {
+            fail_members(c, s, gr, rc);
+            return true;
+        }
     }
     PlanInstance *p = gr->plan.get();
     const int B = p->B;  // <= pending: every colouring of the pass belongs to a request
@@ -387,10 +403,14 @@ void launch_next(Ctx *c, Server *s, Group *gr)
             cudaSuccess)
         rc = fail(CC_ERR_CUDA, "error word read-back failed");
     if (rc == CC_OK && cudaEventRecord(gr->ev, gr->stream) != cudaSuccess) rc = fail(CC_ERR_CUDA, "event record failed");
-    if (rc != CC_OK) return fail_members(c, s, gr, rc);
+    if (rc != CC_OK) {
+        fail_members(c, s, gr, rc);
+        return true;
+    }
     gr->inflight = true;
     s->st.colourings_run += B;
     if (requests >= 2) s->st.shared_passes++;
+    return true;
 }
 
 void worker(Server *s)
@@ -425,10 +445,7 @@ void worker(Server *s)
                         i++;
                     }
                 }
-                if (!gr->members.empty()) {
-                    launch_next(c, s, gr);
-                    progress = true;
-                }
+                if (!gr->members.empty() && launch_next(c, s, gr)) progress = true;
                 if (gr->members.empty() && !gr->inflight) {
                     release_group(c, s, gr);
                     s->groups.erase(s->groups.begin() + gi);

@@ -156,6 +156,25 @@ def test_wide_exact_counts_star_on_star():
     c.close()
 
 
+def test_more_launches_than_work_counters():
+    # one-vertex blocks: the root chain (root 2) gathers the shared table of
+    # the two 4-vertex stars twice, one persistent launch per block each, so
+    # one pass takes more than twice as many persistent launches as there are
+    # blocks -- far more than the 4096 work counters the pass clears at its
+    # start; the counters are cleared again (in stream order) when used up,
+    # and the counts stay exact
+    g = gg.rmat_graph(12, seed=21)
+    k, e = gg.template_edges("caterpillar10")
+    c = make_ctx(block_vertices=1, batch=1, split_threshold=16)
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 2)
+    info = c.plan_info(gid, tid)
+    assert info["n_blocks"] > 2048
+    res = c.count(gid, tid, seed=6, n_iter=1, want_maps=True)
+    assert res["maps"] == oracle_maps(g, k, e, 2, 6, range(1))
+    c.close()
+
+
 # ------------------------------------------------------------------ per-vertex outputs
 
 def test_sampled_vertices_match_oracle_per_vertex():
