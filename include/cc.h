@@ -565,6 +565,15 @@ cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *au
  * Host only. */
 cc_status cc_template_automorphisms_labelled(int32_t k, const int32_t *edges, const uint8_t *labels, int64_t *aut);
 
+/* Canonical form of a tree template (labels[k] or NULL): a NUL-terminated
+ * string, equal for two templates exactly when they are isomorphic (by a
+ * label-preserving map when labelled) -- the key by which the serving loop
+ * lets requests of isomorphic templates share passes (isomorphic templates
+ * have the same counts).  Written to out[cap]; CC_ERR_CAPACITY (nothing
+ * written) when cap is below the form's length + 1.  Host only. */
+cc_status cc_template_canonical_form(int32_t k, const int32_t *edges, const uint8_t *labels, char *out,
+                                     int32_t cap);
+
 /* The rate of 64-bit limb products (a 64 x 64-bit multiply's low and high
  * halves counted as two, each with its carry-propagating add) that the
  * context's GPU sustains on register operands: the arithmetic ceiling of the

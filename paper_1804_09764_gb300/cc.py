@@ -184,6 +184,7 @@ def load_library(path: str = LIB_PATH):
         "cc_template_load_labelled": (I32, [P, I32, P, P, I32, P]),
         "cc_graph_set_labels": (I32, [P, I64, P]),
         "cc_template_automorphisms_labelled": (I32, [I32, P, P, P]),
+        "cc_template_canonical_form": (I32, [I32, P, P, P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -245,6 +246,15 @@ def cc_template_automorphisms_labelled(k: int, edges, labels) -> int:
         raise ValueError("one label per template vertex")
     _check(lib.cc_template_automorphisms_labelled(k, _ptr(e), _ptr(lab), ctypes.byref(a)))
     return a.value
+
+
+def cc_template_canonical_form(k: int, edges, labels=None) -> str:
+    """cc_template_canonical_form: equal strings exactly for isomorphic trees."""
+    lib = load_library()
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib.cc_template_canonical_form(k, _ptr(_edges_array(k, edges)), _ptr(lab), buf, len(buf)))
+    return buf.value.decode()
 
 
 def cc_iterations_for(k: int, epsilon: float, delta: float) -> tuple[int, int]:

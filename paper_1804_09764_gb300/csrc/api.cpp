@@ -611,6 +611,24 @@ cc_status cc_limb_product_rate(cc_ctx *ctx, double *per_second)
     return CC_OK;
 }
 
+cc_status cc_template_canonical_form(int32_t k, const int32_t *edges, const uint8_t *labels, char *out, int32_t cap)
+{
+    if (!out) return fail(CC_ERR_INVALID_ARG, "out is NULL");
+    TemplatePlan tp;
+    std::string err;
+    int rc = build_template_plan(k, edges, 0, 0, 16.0, &tp, &err, labels);  // validates the tree
+    if (rc) return fail(rc, err);
+    std::vector<std::vector<int>> adj(k);
+    for (int i = 0; i + 1 < k; i++) {
+        adj[edges[2 * i]].push_back(edges[2 * i + 1]);
+        adj[edges[2 * i + 1]].push_back(edges[2 * i]);
+    }
+    const std::string f = tree_canonical_form(k, adj, labels);
+    if (cap < (int32_t)f.size() + 1) return fail(CC_ERR_CAPACITY, "needs " + std::to_string(f.size() + 1) + " bytes");
+    std::memcpy(out, f.c_str(), f.size() + 1);
+    return CC_OK;
+}
+
 cc_status cc_template_automorphisms(int32_t k, const int32_t *edges, int64_t *aut)
 {
     if (!aut) return fail(CC_ERR_INVALID_ARG, "aut is NULL");

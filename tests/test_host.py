@@ -211,3 +211,49 @@ def test_c_caller_compiles_and_links_against_the_library(lib, tmp_path):
                            os.path.join(ROOT, "tests", "c_abi_example.c"), "-L", build_dir, "-lcc_gb300",
                            f"-Wl,-rpath,{build_dir}", "-o", str(exe)])
     assert exe.exists()
+
+
+def _isomorphic_brute(k, e1, e2, l1=None, l2=None):
+    """Is there a vertex bijection (label-preserving when labels are given)
+    mapping the edges of e1 onto those of e2?  Plain search over k! maps."""
+    import itertools
+
+    s2 = {frozenset(x) for x in e2}
+    for perm in itertools.permutations(range(k)):
+        if l1 is not None and any(l1[v] != l2[perm[v]] for v in range(k)):
+            continue
+        if all(frozenset((perm[a], perm[b])) in s2 for a, b in e1):
+            return True
+    return False
+
+
+def test_canonical_form_is_the_isomorphism_class(lib):
+    # the key by which served requests of isomorphic templates share passes
+    import itertools
+    import random
+
+    # over all Pruefer sequences on k vertices the forms take as many values
+    # as there are unlabelled trees (Otter: 1, 2, 3, 6, 11 for k = 3..7)
+    for k, want in zip(range(3, 8), [1, 2, 3, 6, 11]):
+        forms = {cc.cc_template_canonical_form(k, gg._prufer_decode(k, seq))
+                 for seq in itertools.product(range(k), repeat=k - 2)}
+        assert len(forms) == want
+    rng = random.Random(17)
+    for i in range(40):
+        k = rng.randrange(4, 8)
+        e1, e2 = gg.prufer_tree(k, 900 + i), gg.prufer_tree(k, 950 + i)
+        perm = list(range(k))
+        rng.shuffle(perm)
+        e1p = [(perm[a], perm[b]) for a, b in e1]
+        assert cc.cc_template_canonical_form(k, e1p) == cc.cc_template_canonical_form(k, e1)
+        same = cc.cc_template_canonical_form(k, e1) == cc.cc_template_canonical_form(k, e2)
+        assert same == _isomorphic_brute(k, e1, e2)
+        # labelled: the forms agree exactly when a label-preserving map exists
+        l1 = [rng.randrange(2) for _ in range(k)]
+        l2 = [rng.randrange(2) for _ in range(k)]
+        same = cc.cc_template_canonical_form(k, e1, l1) == cc.cc_template_canonical_form(k, e1p, l2)
+        l1p = [0] * k
+        for v in range(k):
+            l1p[perm[v]] = l1[v]
+        assert same == _isomorphic_brute(k, e1, e1p, l1, l2)
+        assert cc.cc_template_canonical_form(k, e1p, l1p) == cc.cc_template_canonical_form(k, e1, l1)
