@@ -204,7 +204,12 @@ cc_status open_group(Ctx *c, Server *s, Request *r, const Template *t, std::uniq
         ng->stream = nullptr;
         return fail(CC_ERR_CUDA, "stream creation failed");
     }
-    cc_status rc = plan_group(c, ng.get(), std::min(batch_cap(c), r->job.n_iter));
+    // as many colourings per pass as the request has (up to the cap), halved
+    // while the workspace does not fit
+    const int want = std::min(batch_cap(c), r->job.n_iter);
+    cc_status rc = CC_ERR_BUDGET;
+    for (int w = want; w >= 1 && rc == CC_ERR_BUDGET; w = w > 1 ? w / 2 : 0) rc = plan_group(c, ng.get(), w);
+    ng->planned_for = want;
     if (rc == CC_OK && (cudaMallocHost(&ng->hp, sizeof(ColourParams)) != cudaSuccess ||
                         cudaMallocHost(&ng->ht, (size_t)8 * kHostTotalsWords) != cudaSuccess ||
                         cudaMallocHost(&ng->herr, sizeof(int32_t)) != cudaSuccess ||

@@ -111,3 +111,31 @@ def test_one_launch_carries_two_requests():
     aut = O.automorphisms(k, e2)
     assert got2["counts"][0] == O.count_maps(g, k, e2, 0, seed=12, j=3) // aut
     c.close()
+
+
+def test_served_group_replans_to_a_batch_that_fits():
+    # batch=16 pins the number of colourings a plan takes, and a pass of all
+    # six colourings does not fit this arena: cc_count refuses the count, while
+    # the serving loop re-plans its group with half as many colourings per
+    # pass until the workspace fits; the counts are those of the count alone
+    from paper_1804_09764_gb300 import cc
+
+    g = gg.rmat_graph(12, seed=13)
+    k, e = gg.template_edges("tree12")
+    big = make_ctx(batch=1)
+    gid = big.graph_load(g)
+    tid = big.template_load(k, e, 1)
+    ws1 = big.plan_info(gid, tid)["workspace_bytes"]
+    alone = big.count(gid, tid, seed=31, n_iter=6)["counts"]
+    big.close()
+    c = make_ctx(batch=16, budget_bytes=int(3.5 * ws1) + (96 << 20))
+    gid = c.graph_load(g)
+    tid = c.template_load(k, e, 1)
+    with pytest.raises(cc.CCError) as ei:
+        c.count(gid, tid, seed=31, n_iter=6)
+    assert ei.value.status == -5  # CC_ERR_BUDGET
+    r = c.submit(gid, tid, 31, 6)
+    assert c.wait(r, 6, timeout_s=120)["counts"] == alone
+    st = c.serve_stats()
+    assert st["completed"] == 1 and st["colourings_run"] == 6 and st["passes"] >= 2, st
+    c.close()
