@@ -19,61 +19,97 @@ inline unsigned grid_stride_ctas(int64_t items, int threads)
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
+// Every row of a chain at vertex v is zero at the colour sets without v's own
+// colour col(v): the rooted subtree contains v.  So out[v][S] is zero unless
+// col(v) is in S, and the combines compute only the E = C(k-1, h-1) outputs S
+// that hold col(v) -- elig[c * E + e], e < E, lists the ranks of the h-sets
+// holding colour c in increasing order -- and write zeros at the others
+// (rm_h[S * k + c] == 0xFFFF: c not in S) and in the padding columns.  cv[vb]
+// is col(v) for row vb (vertex-major, colouring-minor, like the rows).
+
+// The sum over the npairs splits of output column s of one row, read from the
+// row's act values ar (La limbs) and aggregate pr (Lb limbs), in groups of G:
+// split entries, then both operands, then the multiply-adds.
+template <int L, int La, int Lb, int G, typename Act, typename Agg>
+__device__ __forceinline__ Wide<L> split_sum(int64_t s, int64_t Ch, int64_t npairs, const uint32_t *__restrict__ pairs,
+                                             Act ar, Agg pr)
+{
+    Wide<L> acc;
+    wzero(acc);
+    const uint32_t *ps = pairs + s;
+    int64_t q0 = 0;
+    for (; q0 + G <= npairs; q0 += G) {
+        uint32_t pq[G];
+#pragma unroll
+        for (int j = 0; j < G; j++) pq[j] = __ldg(ps + (q0 + j) * Ch);
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            Wide<La> x;
+            Wide<Lb> y;
+#pragma unroll
+            for (int l = 0; l < La; l++) x.w[l] = ar[(pq[j] & 0xFFFFu) * La + l];
+#pragma unroll
+            for (int l = 0; l < Lb; l++) y.w[l] = pr[(pq[j] >> 16) * Lb + l];
+            wmac_mixed<L, La, Lb>(acc, x, y);
+        }
+    }
+    for (int64_t q = q0; q < npairs; q++) {
+        const uint32_t pq = __ldg(ps + q * Ch);
+        Wide<La> x;
+        Wide<Lb> y;
+#pragma unroll
+        for (int l = 0; l < La; l++) x.w[l] = ar[(pq & 0xFFFFu) * La + l];
+#pragma unroll
+        for (int l = 0; l < Lb; l++) y.w[l] = pr[(pq >> 16) * Lb + l];
+        wmac_mixed<L, La, Lb>(acc, x, y);
+    }
+    return acc;
+}
+
 // Rows carry Cs >= C columns (C rounded up to even so a row is a whole number of
 // 16-byte units); columns C..Cs-1 are written as zero.  act rows hold La-limb
 // values, agg rows Lb-limb values, out rows L-limb values (La, Lb <= L): each
 // operand is read at the width its bound needs and the product is formed only
-// from the limb products below limb L.
+// from the limb products below limb L.  One thread per output: first the zeros
+// of every row, then the E outputs per row that hold col(v).
 template <int L, int La, int Lb>
-__global__ void combine_generic_kernel(int64_t total, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps,
+__global__ void combine_generic_kernel(int64_t rows, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps,
                                        int64_t npairs, const uint32_t *__restrict__ pairs,
                                        const uint64_t *__restrict__ act, const uint64_t *__restrict__ agg,
-                                       uint64_t *__restrict__ out)
+                                       uint64_t *__restrict__ out, int k, const uint8_t *__restrict__ cv,
+                                       const uint16_t *__restrict__ rm_h, const uint16_t *__restrict__ elig,
+                                       int64_t E)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * Chs; i += stride) {
         const int64_t vb = i / Chs, s = i - vb * Chs;
-        Wide<L> acc;
-        wzero(acc);
-        if (s < Ch) {
-            const uint64_t *ar = act + vb * Cas * La;
-            const uint64_t *pr = agg + vb * Cps * Lb;
-            // in groups of G: split entries, then both operands, then the multiply-adds
-            constexpr int G = L <= 1 ? 4 : 2;
-            for (int64_t q0 = 0; q0 < npairs; q0 += G) {
-                uint32_t pq[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) pq[j] = q0 + j < npairs ? __ldg(pairs + (q0 + j) * Ch + s) : 0u;
-                Wide<La> x[G];
-                Wide<Lb> y[G];
-#pragma unroll
-                for (int j = 0; j < G; j++) {
-                    if (q0 + j < npairs) {
-                        x[j] = wload<La, La>(ar + (pq[j] & 0xFFFFu) * La);
-                        y[j] = wload<Lb, Lb>(pr + (pq[j] >> 16) * Lb);
-                    } else {
-                        wzero(x[j]);
-                        wzero(y[j]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < G; j++) wmac_mixed<L, La, Lb>(acc, x[j], y[j]);
-            }
+        if (s >= Ch || rm_h[s * k + cv[vb]] == 0xFFFFu) {
+            Wide<L> z;
+            wzero(z);
+            wstore(out + i * L, z);
         }
-        wstore(out + i * L, acc);
+    }
+    constexpr int G = L <= 1 ? 4 : 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * E; i += stride) {
+        const int64_t vb = i / E, e = i - vb * E;
+        const int64_t s = elig[(int64_t)cv[vb] * E + e];
+        const Wide<L> acc = split_sum<L, La, Lb, G>(s, Ch, npairs, pairs, act + vb * Cas * La, agg + vb * Cps * Lb);
+        wstore(out + (vb * Chs + s) * L, acc);
     }
 }
 
 // The same combine with one CTA per (vertex, colouring) row at a time: the
 // row's act values (Cas x La words) and aggregate (Cps x Lb words) are staged
-// in shared memory, then its threads compute every output of the row from
-// there.  Used for large rows, whose random act reads would otherwise miss L1
+// in shared memory, then its threads compute the row's outputs from there.
+// Used for large rows, whose random act reads would otherwise miss L1
 // (several rows of ~100 KB per SM).
 template <int L, int La, int Lb>
 __global__ void __launch_bounds__(512)
 combine_generic_smem_kernel(int64_t rows, int64_t Ch, int64_t Chs, int64_t Cas, int64_t Cps, int64_t npairs,
                             const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
-                            const uint64_t *__restrict__ agg, uint64_t *__restrict__ out)
+                            const uint64_t *__restrict__ agg, uint64_t *__restrict__ out, int k,
+                            const uint8_t *__restrict__ cv, const uint16_t *__restrict__ rm_h,
+                            const uint16_t *__restrict__ elig, int64_t E)
 {
     extern __shared__ uint64_t sm[];
     uint64_t *sa = sm, *sp = sm + Cas * La;
@@ -83,42 +119,21 @@ combine_generic_smem_kernel(int64_t rows, int64_t Ch, int64_t Chs, int64_t Cas, 
         const uint64_t *pr = agg + vb * Cps * Lb;
         for (int64_t i = threadIdx.x; i < Cas * La; i += blockDim.x) sa[i] = __ldg(ar + i);
         for (int64_t i = threadIdx.x; i < Cps * Lb; i += blockDim.x) sp[i] = __ldg(pr + i);
-        __syncthreads();
-        for (int64_t s = threadIdx.x; s < Chs; s += blockDim.x) {
-            Wide<L> acc;
-            wzero(acc);
-            if (s < Ch) {
-                // split entries G at a time (all G global loads in flight before
-                // the shared-memory operand reads and multiply-adds that need them)
-                constexpr int G = L <= 2 ? 8 : 4;
-                const uint32_t *ps = pairs + s;
-                int64_t q0 = 0;
-                for (; q0 + G <= npairs; q0 += G) {
-                    uint32_t pq[G];
-#pragma unroll
-                    for (int j = 0; j < G; j++) pq[j] = __ldg(ps + (q0 + j) * Ch);
-#pragma unroll
-                    for (int j = 0; j < G; j++) {
-                        Wide<La> x;
-                        Wide<Lb> y;
-#pragma unroll
-                        for (int l = 0; l < La; l++) x.w[l] = sa[(pq[j] & 0xFFFFu) * La + l];
-#pragma unroll
-                        for (int l = 0; l < Lb; l++) y.w[l] = sp[(pq[j] >> 16) * Lb + l];
-                        wmac_mixed<L, La, Lb>(acc, x, y);
-                    }
-                }
-                for (int64_t q = q0; q < npairs; q++) {
-                    const uint32_t pq = __ldg(ps + q * Ch);
-                    Wide<La> x;
-                    Wide<Lb> y;
-#pragma unroll
-                    for (int l = 0; l < La; l++) x.w[l] = sa[(pq & 0xFFFFu) * La + l];
-#pragma unroll
-                    for (int l = 0; l < Lb; l++) y.w[l] = sp[(pq >> 16) * Lb + l];
-                    wmac_mixed<L, La, Lb>(acc, x, y);
-                }
+        const int c = cv[vb];
+        for (int64_t s = threadIdx.x; s < Chs; s += blockDim.x)
+            if (s >= Ch || rm_h[s * k + c] == 0xFFFFu) {
+                Wide<L> z;
+                wzero(z);
+                wstore(out + (vb * Chs + s) * L, z);
             }
+        __syncthreads();
+        // split entries G at a time (all G global loads in flight before the
+        // shared-memory operand reads and multiply-adds that need them)
+        constexpr int G = L <= 2 ? 8 : 4;
+        for (int64_t e = threadIdx.x; e < E; e += blockDim.x) {
+            const int64_t s = elig[(int64_t)c * E + e];
+            const Wide<L> acc = split_sum<L, La, Lb, G>(s, Ch, npairs, pairs, (const uint64_t *)sa,
+                                                        (const uint64_t *)sp);
             wstore(out + (vb * Chs + s) * L, acc);
         }
     }
@@ -178,7 +193,8 @@ double limb_product_rate(cudaStream_t st, uint64_t *scratch)
 
 void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, int B, int64_t Ch, int64_t Chs,
                             int64_t Cas, int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
-                            const uint64_t *agg, uint64_t *out)
+                            const uint64_t *agg, uint64_t *out, int k, const uint8_t *cv, const uint16_t *rm_h,
+                            const uint16_t *elig, int64_t E)
 {
     const int64_t total = nv * B * Chs;
     if (total == 0) return;
@@ -205,9 +221,11 @@ void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, 
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 512, smem);                 \
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                      \
             const int64_t gs = std::min<int64_t>(rows, (int64_t)std::max(1, per_sm) * sms);         \
-            kfn<<<(unsigned)gs, 512, smem, st>>>(rows, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out); \
+            kfn<<<(unsigned)gs, 512, smem, st>>>(rows, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out, k, cv, rm_h, \
+                                                 elig, E);                                                       \
         } else {                                                                                    \
-            combine_generic_kernel<l, a, b><<<g, 256, 0, st>>>(total, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out); \
+            combine_generic_kernel<l, a, b><<<g, 256, 0, st>>>(rows, Ch, Chs, Cas, Cps, npairs, pairs, act, agg, out, \
+                                                               k, cv, rm_h, elig, E);                                 \
         }                                                                                           \
         break;
     switch ((L - 1) * 16 + (La - 1) * 4 + (Lb - 1)) {

@@ -580,7 +580,17 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
             if (s.a >= 2) need_pairs.push_back({s.h, s.a});  // p = 1 steps use the (h, h-1) table
     std::sort(need_pairs.begin(), need_pairs.end());
     need_pairs.erase(std::unique(need_pairs.begin(), need_pairs.end()), need_pairs.end());
+    // per set size h: for each colour, the ranks of the h-sets holding it
+    // (k * C(k-1, h-1) entries; k * 2^(k-1) over all h)
+    std::map<int, std::vector<uint16_t>> elig;
+    for (int h = 1; h <= k; h++) {
+        std::vector<uint16_t> &el = elig[h];
+        for (int cc = 0; cc < k; cc++)
+            for (int64_t r = 0; r < binom(k, h); r++)
+                if (T.mask_of_rank[h][r] >> cc & 1) el.push_back((uint16_t)r);
+    }
     uint64_t cbytes = 0;
+    for (auto &kv : elig) cbytes += rup(kv.second.size() * 2);
     for (int h = 1; h <= k; h++) cbytes += rup(T.rm[h].size() * 2);
     for (int q = 0; q < k; q++) cbytes += rup(T.ad[q].size() * 2);
     std::vector<std::vector<uint32_t>> pt;
@@ -602,6 +612,12 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
         p->d_ad[q] = (uint16_t *)cp;
         CC_CUDA(cudaMemcpyAsync(cp, T.ad[q].data(), T.ad[q].size() * 2, cudaMemcpyHostToDevice, st));
         cp += rup(T.ad[q].size() * 2);
+    }
+    p->d_elig.clear();
+    for (auto &kv : elig) {
+        p->d_elig[kv.first] = (uint16_t *)cp;
+        CC_CUDA(cudaMemcpyAsync(cp, kv.second.data(), kv.second.size() * 2, cudaMemcpyHostToDevice, st));
+        cp += rup(kv.second.size() * 2);
     }
     for (size_t i = 0; i < need_pairs.size(); i++) {
         p->d_pairs[need_pairs[i]] = (uint32_t *)cp;
@@ -863,6 +879,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 auto vstride = [&](size_t j, int64_t cs) { return j == nleaf ? (int64_t)B * cs * L : slot; };
                 LeafChain lc{};
                 lc.n = (int)nleaf;
+                lc.col = col;
                 for (size_t j = 1; j <= nleaf; j++) {
                     int64_t cs;
                     lc.out[j - 1] = step_out(j, &cs);
@@ -872,6 +889,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     lc.vs[j - 1] = vstride(j, cs);
                     lc.pairs[j - 1] = p->d_pairs.at({C.steps[j].h, C.steps[j].a});
                     lc.rm[j - 1] = p->d_rm[C.steps[j].h];
+                    lc.elig[j - 1] = p->d_elig.at(C.steps[j].h);
+                    lc.E[j - 1] = (int)binom(k - 1, C.steps[j].h - 1);
                     lc.hist[j - 1] = hist_for(C.steps[j].leaf_label);
                 }
                 const int64_t nh = hv.h1 - hv.h0;
@@ -927,7 +946,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     int64_t prev_s = Chs0;
                     for (int j = 0; j < lc.n; j++) {
                         launch_combine_hist(st, L, L, nh, B, k, lc.Ch[j], lc.Chs[j], prev_s, lc.h[j], lc.pairs[j],
-                                            prev, lc.hist[j] + (uint64_t)v0 * B * k, lc.out[j]);
+                                            prev, lc.hist[j] + (uint64_t)v0 * B * k, lc.out[j], col + (uint64_t)v0 * B,
+                                            lc.rm[j], lc.elig[j], lc.E[j]);
                         prev = lc.out[j];
                         prev_s = lc.Chs[j];
                     }
@@ -952,7 +972,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         note_path(si, CC_PATH_LEAF_COMBINE, La, 0, Lo);
                         Ln.begin(K_CHIST);
                         launch_combine_hist(st, Lo, La, nv, B, k, Ch, Chs, cur_stride, s.h, p->d_pairs.at({s.h, s.a}),
-                                            cur, hrow, out);
+                                            cur, hrow, out, col + (uint64_t)v0 * B, p->d_rm[s.h], p->d_elig.at(s.h),
+                                            binom(k - 1, s.h - 1));
                         Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + binom(k, s.a) * 8.0 * La + 4.0 * k));
                     }
                 } else if (c->opt.fused && s.a == 1 && !s.reuse_agg &&
@@ -1102,7 +1123,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         note_path(si, CC_PATH_GATHER_COMBINE, Ls, Lg, Lo);
                         Ln.begin(K_COMBINE);
                         launch_combine_generic(st, Lo, La, Lg, nv, B, Ch, Chs, cur_stride, Cps, binom(s.h, s.a),
-                                               p->d_pairs.at({s.h, s.a}), cur, agg, out);
+                                               p->d_pairs.at({s.h, s.a}), cur, agg, out, k, col + (uint64_t)v0 * B,
+                                               p->d_rm[s.h], p->d_elig.at(s.h), binom(k - 1, s.h - 1));
                         Ln.end(1, (double)nv * B * (Ch * 8.0 * Lo + binom(k, s.a) * 8.0 * La + Cp * 8.0 * Lg));
                     }
                 }

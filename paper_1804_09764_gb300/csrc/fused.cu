@@ -101,7 +101,13 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
 // The chain's p = 1 steps for vertex v, from its first-step row orow (stride
 // Chs per colouring, Lf-limb values; Lf <= Ld): out_j[S] = sum over c in S of
 // out_{j-1}[S \ {c}] * hist[v][c], written with Ld limbs.  The warp reads in
-// step j the rows its lanes wrote in step j - 1 (__syncwarp).  Only the
+// step j the rows its lanes wrote in step j - 1 (__syncwarp).
+// Every row of the chain is zero at the sets without v's own colour col(v)
+// (the rooted subtree contains v), so a step computes only the C(k-1, h-1)
+// outputs S holding col(v) (chain.elig), and of their terms only those with
+// c != col(v) (prev[S \ {col(v)}] lacks col(v)); the sets a step reads are
+// therefore all ones holding col(v), and only the chain's table (the last
+// step, read in full by later gathers) gets its zeros written.  Only the
 // colours that some neighbour of v has (in any colouring of the pass) give
 // non-zero terms: when they are fewer than half of |S| the sum runs over them
 // (rm_h[S * k + c]: rank of S \ {c}, or c outside S), otherwise over the
@@ -114,6 +120,7 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
     const uint64_t *prev = orow;
     int prev_s = Chs;
     const int Bk = B * k;
+    const uint8_t *cv = chain.col + v * B;
     for (int j = 0; j < chain.n; j++) {
         const uint32_t *hr = chain.hist[j] + v * (int64_t)Bk;
         // neighbour colour counts; with B * k <= 32 they stay in the lanes'
@@ -124,22 +131,35 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
             if ((t < 32 ? hv : hr[t]) != 0) nz |= 1u << (t % k);
         nz = __reduce_or_sync(0xffffffffu, nz);
         __syncwarp();
-        const int cj = (int)chain.Ch[j], csj = (int)chain.Chs[j], hj = chain.h[j];
+        const int cj = (int)chain.Ch[j], csj = (int)chain.Chs[j], hj = chain.h[j], E = chain.E[j];
         const bool sparse = 2 * __popc(nz) < hj;
         const uint16_t *__restrict__ rm = chain.rm[j];
+        const uint16_t *__restrict__ el = chain.elig[j];
         const uint32_t *__restrict__ pt = chain.pairs[j];
         uint64_t *dst = chain.out[j] + (v - v0) * chain.vs[j];
         const int Lp = j == 0 ? Lf : Ld;  // limbs of the rows read
+        if (j + 1 == chain.n) {
+            // the chain's table: zeros at the sets without col(v) and in the padding
+            RowPos zp;
+            zp.init(lane, csj);
+            for (int i = lane; i < B * csj; i += 32, zp.step(32, csj))
+                if (zp.s >= cj || rm[zp.s * k + cv[zp.b]] == 0xFFFFu) {
+                    Wide<Ld> z;
+                    wzero(z);
+                    wstore(dst + (int64_t)i * Ld, z);
+                }
+        }
         // count of colour c among the neighbours, colouring b (all lanes call it)
         auto count_of = [&](int b, int c, bool live) -> uint32_t {
             if (Bk <= 32) return __shfl_sync(0xffffffffu, hv, (b * k + c) & 31);
             return live ? hr[b * k + c] : 0u;
         };
-        RowPos pos;
-        pos.init(lane, csj);
-        for (int i0 = 0; i0 < B * csj; i0 += 32, pos.step(32, csj)) {
-            const int i = i0 + lane;
-            const bool live = i < B * csj && pos.s < cj;
+        RowPos pos;  // (colouring, index among the E sets holding its col(v))
+        pos.init(lane, E);
+        for (int i0 = 0; i0 < B * E; i0 += 32, pos.step(32, E)) {
+            const bool live = i0 + lane < B * E;
+            const int cb = live ? cv[pos.b] : 0;  // col(v) in this lane's colouring
+            const int S = live ? el[cb * E + pos.s] : 0;
             const uint64_t *ar = prev + (int64_t)pos.b * prev_s * Lp;
             Wide<Ld> acc;
             wzero(acc);
@@ -147,7 +167,7 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
                 for (unsigned m = nz; m; m &= m - 1) {
                     const int c = __ffs(m) - 1;
                     const uint32_t hc = count_of(pos.b, c, live);
-                    const uint32_t r = live ? rm[pos.s * k + c] : 0xFFFFu;
+                    const uint32_t r = live && c != cb ? rm[S * k + c] : 0xFFFFu;
                     if (r != 0xFFFFu && hc) {
                         Wide<Ld> a;
 #pragma unroll
@@ -159,11 +179,11 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
                 for (int q0 = 0; q0 < hj; q0 += QB) {
                     uint32_t pq[QB], hc[QB];
 #pragma unroll
-                    for (int t = 0; t < QB; t++) pq[t] = live && q0 + t < hj ? __ldg(pt + (q0 + t) * cj + pos.s) : 0u;
+                    for (int t = 0; t < QB; t++) pq[t] = live && q0 + t < hj ? __ldg(pt + (q0 + t) * cj + S) : 0u;
 #pragma unroll
                     for (int t = 0; t < QB; t++) {
                         hc[t] = count_of(pos.b, (int)(pq[t] >> 16), live);
-                        if (!(live && q0 + t < hj)) hc[t] = 0;
+                        if (!(live && q0 + t < hj) || (int)(pq[t] >> 16) == cb) hc[t] = 0;
                     }
                     Wide<Ld> a[QB];
 #pragma unroll
@@ -176,7 +196,7 @@ __device__ __forceinline__ void leaf_steps(int64_t v, int64_t v0, const uint64_t
                         if (hc[t]) wmac_small(acc, a[t], hc[t]);
                 }
             }
-            if (i < B * csj) wstore(dst + (int64_t)i * Ld, acc);
+            if (live) wstore(dst + ((int64_t)pos.b * csj + S) * Ld, acc);
         }
         prev = dst;
         prev_s = csj;
@@ -206,7 +226,7 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
         if (e1 - e0 <= split) {  // heavy vertices: tasks, reduce, select, p = 1 kernels
             uint64_t *orow = out + (v - v0) * out_vs;
             const uint8_t *cv = col + v * B;
-            zero_missing<Lf>(orow, B, k, Ch, Chs, rm_h, cv, lane);
+            // (no zeros: the leaf steps read this row only at sets holding col(v))
             RowPos pos;
             pos.init(lane, Cps);
             for (int base = 0; base < R; base += 32 * VPT) {

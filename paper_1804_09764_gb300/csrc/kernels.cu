@@ -677,26 +677,39 @@ __global__ void select_heavy_kernel(int64_t h0, int64_t h1, int64_t v0, const in
 
 // act rows hold La-limb values (La <= L)
 template <int L, int La>
-__global__ void combine_hist_kernel(int64_t total, int k, int64_t Ch, int64_t Chs, int64_t Cas, int h,
+__global__ void combine_hist_kernel(int64_t rows, int k, int64_t Ch, int64_t Chs, int64_t Cas, int h,
                                     const uint32_t *__restrict__ pairs, const uint64_t *__restrict__ act,
-                                    const uint32_t *__restrict__ hist, uint64_t *__restrict__ out)
+                                    const uint32_t *__restrict__ hist, uint64_t *__restrict__ out,
+                                    const uint8_t *__restrict__ cv, const uint16_t *__restrict__ rm_h,
+                                    const uint16_t *__restrict__ elig, int64_t E)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    // zeros at the sets without the row's vertex colour and in the padding,
+    // then the E outputs per row that hold it (the act rows are zero at sets
+    // without it: the rooted subtree contains the vertex)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * Chs; i += stride) {
         const int64_t vb = i / Chs, s = i - vb * Chs;
+        if (s >= Ch || rm_h[s * k + cv[vb]] == 0xFFFFu) {
+            Wide<L> z;
+            wzero(z);
+            wstore(out + i * L, z);
+        }
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * E; i += stride) {
+        const int64_t vb = i / E, e = i - vb * E;
+        const int c = cv[vb];
+        const int64_t s = elig[(int64_t)c * E + e];
         Wide<L> acc;
         wzero(acc);
-        if (s < Ch) {
-            const uint64_t *ar = act + vb * Cas * La;
-            const uint32_t *hr = hist + vb * k;
+        const uint64_t *ar = act + vb * Cas * La;
+        const uint32_t *hr = hist + vb * k;
 #pragma unroll 4
-            for (int q = 0; q < h; q++) {
-                const uint32_t pq = __ldg(pairs + q * Ch + s);
-                const uint32_t hc = hr[pq >> 16];
-                if (hc) wmac_small(acc, wload<La, L>(ar + (pq & 0xFFFFu) * La), hc);
-            }
+        for (int q = 0; q < h; q++) {
+            const uint32_t pq = __ldg(pairs + q * Ch + s);
+            const uint32_t hc = (int)(pq >> 16) == c ? 0u : hr[pq >> 16];  // S \ {col(v)} lacks col(v)
+            if (hc) wmac_small(acc, wload<La, L>(ar + (pq & 0xFFFFu) * La), hc);
         }
-        wstore(out + i * L, acc);
+        wstore(out + (vb * Chs + s) * L, acc);
     }
 }
 
@@ -1173,7 +1186,7 @@ void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0,
 
 void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int k, int64_t Ch, int64_t Chs,
                          int64_t Cas, int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist,
-                         uint64_t *out)
+                         uint64_t *out, const uint8_t *cv, const uint16_t *rm_h, const uint16_t *elig, int64_t E)
 {
     const int64_t total = nv * B * Chs;
     if (total == 0) return;
@@ -1183,7 +1196,8 @@ void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int 
     note_launch("combine_hist_kernel", L, La);
 #define CC_CH(l, a)                                                                                        \
     case ((l - 1) * 4 + (a - 1)):                                                                          \
-        combine_hist_kernel<l, a><<<g, 256, 0, st>>>(total, k, Ch, Chs, Cas, h, pairs, act, hist, out); \
+        combine_hist_kernel<l, a><<<g, 256, 0, st>>>(nv * B, k, Ch, Chs, Cas, h, pairs, act, hist, out, cv, rm_h, \
+                                                     elig, E);                                                       \
         break;
     switch ((L - 1) * 4 + (La - 1)) {
         CC_CH(1, 1) CC_CH(2, 1) CC_CH(2, 2) CC_CH(3, 1) CC_CH(3, 2) CC_CH(3, 3)

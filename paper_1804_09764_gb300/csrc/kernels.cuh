@@ -106,9 +106,13 @@ void launch_gather_reduce(cudaStream_t st, int Ld, int64_t h0, int64_t h1, int64
 // output columns are written as zero); B rows per vertex.
 // act rows of La-limb values, agg rows of Lb-limb values, out rows of L limbs
 // (La, Lb <= L)
+// cv: colours of the block's rows ([vertex][colouring]); rm_h: the rank table
+// of size-h sets; elig: for each colour c the E = C(k-1, h-1) ranks of the
+// h-sets holding c, increasing (only those outputs can be non-zero)
 void launch_combine_generic(cudaStream_t st, int L, int La, int Lb, int64_t nv, int B, int64_t Ch, int64_t Chs,
                             int64_t Cas, int64_t Cps, int64_t npairs, const uint32_t *pairs, const uint64_t *act,
-                            const uint64_t *agg, uint64_t *out);
+                            const uint64_t *agg, uint64_t *out, int k, const uint8_t *cv, const uint16_t *rm_h,
+                            const uint16_t *elig, int64_t E);
 // a = 1: act is the single vertex v with colour col(v)
 void launch_combine_select(cudaStream_t st, int L, bool agg_is_hist, int64_t v0, int64_t nv, int B, int k,
                            int64_t Ch, int64_t Chs, int64_t Cps, const uint16_t *rm, const uint8_t *col,
@@ -122,7 +126,7 @@ double limb_product_rate(cudaStream_t st, uint64_t *scratch);
 // act rows of La-limb values (La <= L)
 void launch_combine_hist(cudaStream_t st, int L, int La, int64_t nv, int B, int k, int64_t Ch, int64_t Chs,
                          int64_t Cas, int h, const uint32_t *pairs, const uint64_t *act, const uint32_t *hist,
-                         uint64_t *out);
+                         uint64_t *out, const uint8_t *cv, const uint16_t *rm_h, const uint16_t *elig, int64_t E);
 
 // Fused table gather + a = 1 combine for the light vertices of [v0, v1) (persistent
 // warps on the zeroed counter `next`): out[v][b][T u {col}] = sum_u X[u][b][T].
@@ -149,6 +153,9 @@ struct LeafChain {
     const uint16_t *rm[15];      // rank of S \ {c} per (S, c) of size h, 0xFFFF when c is not in S
     const uint32_t *hist[15];    // colour histograms of the leaf's label (or of all neighbours)
     uint64_t *out[15];
+    const uint16_t *elig[15];    // per colour c, the E ranks of the size-h sets holding c
+    int E[15];                   // C(k-1, h-1)
+    const uint8_t *col;          // colours of the pass, [vertex][colouring]
 };
 // Lf: limbs of the fused step's sums and rows (Ld or Ld - 1); Ld: the leaf steps'
 void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t v0, int64_t v1, int64_t split,

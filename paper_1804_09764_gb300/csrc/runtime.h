@@ -136,6 +136,7 @@ struct PlanInstance {
     std::vector<uint16_t *> d_rm;               // [h]
     std::vector<uint16_t *> d_ad;               // [p] (fused gather + select steps)
     std::map<std::pair<int, int>, uint32_t *> d_pairs;
+    std::map<int, uint16_t *> d_elig;           // [h]: per colour, the ranks of the h-sets holding it
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;
     // workspace of the same plan with every table kept for the whole pass, with
