@@ -283,10 +283,12 @@ typedef struct cc_plan_info {
     uint64_t workspace_bytes;
     int64_t table4_memory, table4_computation;  /* Table 4 cost numbers of the partition */
     double limb_products_per_colouring;  /* 64-bit limb multiplications of the general combines
-                                            (a >= 2, p >= 2) at their widths: per product of an
-                                            La-limb by an Lb-limb value into L limbs, the limb
-                                            pairs i + j < L (low halves) and i + j + 1 < L (high
-                                            halves) */
+                                            (a >= 2, p >= 2) at their widths, over every output
+                                            of Eq. 1: per product of an La-limb by an Lb-limb
+                                            value into L limbs, the limb pairs i + j < L (low
+                                            halves) and i + j + 1 < L (high halves).  (The
+                                            kernels compute only the outputs whose colour set
+                                            holds the vertex's own colour, h/k of a step's.) */
     int64_t split_threshold;         /* neighbour-list task size s in use (Algorithm 4) */
     int64_t block_vertices;          /* vertices per streamed block in use */
     int32_t col_chunks;              /* column segments in use (cc_options.col_chunks meaning) */
