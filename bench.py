@@ -873,7 +873,13 @@ def main():
                    "template": wl["template"], "k": k, "root": info["root"], "colourings_per_step": n_iter,
                    "labels": wl.get("labels", 0),
                    "batch": info["batch"], "blocks": info["n_blocks"], "limbs_root": info["limbs_root"],
-                   "workspace_gb": info["workspace_bytes"] / 1e9, "l2": "inputs larger than L2",
+                   "workspace_gb": info["workspace_bytes"] / 1e9,
+                   # the same plan's device memory without freeing tables early, without
+                   # vertex blocks, and with neither (no memory is allocated for these)
+                   "workspace_no_reuse_gb": info["workspace_no_reuse_bytes"] / 1e9,
+                   "workspace_no_blocks_gb": info["workspace_no_blocks_bytes"] / 1e9,
+                   "workspace_naive_gb": info["workspace_naive_bytes"] / 1e9,
+                   "l2": "inputs larger than L2",
                    "updates_per_colouring": info["updates_per_colouring"],
                    "algorithmic_bytes_per_colouring": info["algorithmic_bytes_per_colouring"],
                    "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused), "autotune": bool(args.autotune),
