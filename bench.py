@@ -690,6 +690,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-max-scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--full-rows", type=int, default=0,
+                    help="1: gathers read whole neighbour rows (0: skip the entries zero by Eq. 1 at batch 1)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n_iter:
@@ -741,7 +743,7 @@ def main():
     ctx = cc.Context(device=local, budget_bytes=budget, timing=1, split_threshold=args.split, batch=args.batch,
                      block_vertices=args.block, gather_mode=args.gather_mode, fused=args.fused,
                      autotune=args.autotune, vertex_order=args.vertex_order, col_chunks=args.col_chunks,
-                     l2_persist_mb=args.l2_persist_mb)
+                     l2_persist_mb=args.l2_persist_mb, full_rows=args.full_rows)
     gid = ctx.graph_load(g)
     tlab = glab = None
     if wl.get("labels"):
@@ -885,6 +887,10 @@ def main():
                    "graph_gen_s": round(gen_s, 1), "wall_s": round(wall, 3), "fused": bool(args.fused), "autotune": bool(args.autotune),
                    "vertex_order": "degree" if args.vertex_order == 0 else "input",
                    "col_chunks": args.col_chunks or "auto", "l2_persist_mb": args.l2_persist_mb,
+                   # entries of a neighbour's row whose set lacks its colour (zero by Eq. 1):
+                   # skipped by the gathers in one-colouring passes, or read with the row
+                   "absent_entries": "skipped" if any("neighbour_colours_kernel" in v for v in insts.values())
+                   else "read",
                    "gather": {0: "bulk-copy (TMA)", 1: "persistent warp per row, 4 rows in flight",
                               2: "warp (16-byte vectors)", 3: "group (row per 32-256 threads)",
                               4: "persistent warp + L2 prefetch", 5: "warp per row, one pass",

@@ -114,7 +114,14 @@ typedef struct cc_options {
                                   window covers the first l2_persist_mb MiB of the source
                                   table, where degree ordering puts the hub rows (persisting
                                   hits, streaming misses); 0 (default): no window */
-    int32_t reserved[2];
+    int32_t full_rows;         /* 0 (default): in passes of one colouring (batch 1, k <= 16,
+                                  fewer than 2^27 active vertices) the table gathers load
+                                  only the entries of a neighbour's row whose colour set
+                                  holds that neighbour's colour -- the others are zero by
+                                  Eq. 1, since the subtree's root is mapped to the
+                                  neighbour -- using a per-pass array of one colour byte
+                                  per adjacency entry; 1: every gather reads whole rows */
+    int32_t reserved[1];
 } cc_options;
 
 void cc_default_options(cc_options *opt);

@@ -52,7 +52,8 @@ class cc_options(ctypes.Structure):
                 ("block_vertices", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("autotune", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("gather_mode", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
-                ("col_chunks", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("col_chunks", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32), ("full_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class cc_result(ctypes.Structure):
@@ -290,7 +291,7 @@ class Context:
     def __init__(self, device: int = 0, budget_bytes: Optional[int] = None, width_bits: int = 0,
                  split_threshold: int = 0, batch: int = 0, block_vertices: int = 0, use_cuda_graph: int = 0,
                  fused: int = 1, autotune: int = 0, max_slots: int = 4, timing: int = 0, gather_mode: int = 1,
-                 vertex_order: int = 0, col_chunks: int = 0, l2_persist_mb: int = 0, stream=None):
+                 vertex_order: int = 0, col_chunks: int = 0, l2_persist_mb: int = 0, full_rows: int = 0, stream=None):
         import torch
 
         lib = load_library()
@@ -323,6 +324,7 @@ class Context:
         opt.vertex_order = vertex_order
         opt.col_chunks = col_chunks
         opt.l2_persist_mb = l2_persist_mb
+        opt.full_rows = full_rows
         torch.cuda.synchronize(device)
         h = ctypes.c_void_p()
         _check(lib.cc_create(ctypes.byref(h), ctypes.byref(opt)))

@@ -178,7 +178,7 @@ static int64_t fused_split(int col_chunks, int64_t v0, int64_t v1, int64_t R, in
 struct Layout {
     uint64_t bytes = 0;
     uint64_t off_col, off_hist, off_act[2], off_agg, off_partial, off_root, off_scratch, off_totals, off_params,
-        off_err, off_ctr;
+        off_err, off_ctr, off_ncol = ~0ull;
     std::vector<uint64_t> off_table;
     int64_t max_tasks = 0;
     std::vector<std::pair<int64_t, int64_t>> blocks;
@@ -256,6 +256,8 @@ Layout layout_for(const PlanInstance &p, const Graph &g, const Graph::Split &sp,
         }
     const int Lm = p.Lmax;
     Lo.off_col = take((uint64_t)n * B);
+    // neighbour colours of a one-colouring pass (AbsentSkip): one byte per list entry
+    if (p.absent_skip && B == 1 && g.nnz > 0) Lo.off_ncol = take((uint64_t)g.nnz);
     Lo.off_hist = need_hist ? take((uint64_t)n * B * k * 4 * std::max<size_t>(1, p.hist_labels.size())) : 0;
     Lo.off_act[0] = take((uint64_t)V * B * maxAct * 8 * Lm);
     Lo.off_act[1] = take((uint64_t)V * B * maxAct * 8 * Lm);
@@ -494,6 +496,13 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     p->width_bits = width_bits;
     p->exact = width_bits == 0;
     p->Lmax = *std::max_element(p->chain_L.begin(), p->chain_L.end());
+    // gathers skip a neighbour's entries whose set lacks its colour (AbsentSkip):
+    // colour masks fit 16 bits, ids 27 (the colour rides above them), and the
+    // plan has a gathered table
+    bool gathers = false;
+    for (auto &C : tp.chains)
+        for (auto &s : C.steps) gathers = gathers || s.src_chain >= 0;
+    p->absent_skip = !c->opt.full_rows && k <= 16 && g->n_act < (int64_t(1) << 27) && gathers;
     // split threshold and batch / block size under the budget
     // default s = 4096: measured on R-MAT s22 / tree-12 (ms per step) 1024: 5590,
     // 2048: 5484, 4096: 5349, 8192: 5368, 16384: 5422, 65536: 6409 -- fewer
@@ -556,6 +565,7 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
     p->ws_no_blocks = layout_for(*p, *g, sp, p->B, n).bytes;
     p->ws_naive = layout_for(*p, *g, sp, p->B, n, true).bytes;
     p->off_col = Lo.off_col;
+    p->off_ncol = Lo.off_ncol;
     p->off_hist = Lo.off_hist;
     p->off_act[0] = Lo.off_act[0];
     p->off_act[1] = Lo.off_act[1];
@@ -589,7 +599,14 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
             for (int64_t r = 0; r < binom(k, h); r++)
                 if (T.mask_of_rank[h][r] >> cc & 1) el.push_back((uint16_t)r);
     }
+    // per set size h: the colour mask of each column of a row (0 for the padding)
+    std::vector<std::vector<uint16_t>> smask(k + 1);
+    for (int h = 1; h <= k; h++) {
+        smask[h].assign(col_stride(binom(k, h)), 0);
+        for (int64_t r = 0; r < binom(k, h); r++) smask[h][r] = (uint16_t)T.mask_of_rank[h][r];
+    }
     uint64_t cbytes = 0;
+    for (int h = 1; h <= k; h++) cbytes += rup(smask[h].size() * 2);
     for (auto &kv : elig) cbytes += rup(kv.second.size() * 2);
     for (int h = 1; h <= k; h++) cbytes += rup(T.rm[h].size() * 2);
     for (int q = 0; q < k; q++) cbytes += rup(T.ad[q].size() * 2);
@@ -612,6 +629,12 @@ cc_status finish_plan(Ctx *c, Graph *g, PlanInstance *p, int n_iter, int width_b
         p->d_ad[q] = (uint16_t *)cp;
         CC_CUDA(cudaMemcpyAsync(cp, T.ad[q].data(), T.ad[q].size() * 2, cudaMemcpyHostToDevice, st));
         cp += rup(T.ad[q].size() * 2);
+    }
+    p->d_smask.assign(k + 1, nullptr);
+    for (int h = 1; h <= k; h++) {
+        p->d_smask[h] = (uint16_t *)cp;
+        CC_CUDA(cudaMemcpyAsync(cp, smask[h].data(), smask[h].size() * 2, cudaMemcpyHostToDevice, st));
+        cp += rup(smask[h].size() * 2);
     }
     p->d_elig.clear();
     for (auto &kv : elig) {
@@ -802,6 +825,24 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
     Ln.begin(K_COLOUR);
     launch_colour(st, g->n_act, B, k, g->orig, (const ColourParams *)W(p->off_params), col);
     Ln.end(1, (double)g->n_act * (8 + B));
+    // one colouring per pass: the gathers load only the entries of a neighbour's
+    // row whose colour set holds the neighbour's colour (the rest are zero)
+    const uint8_t *ncol = nullptr;
+    if (p->off_ncol != ~0ull && B == 1) {
+        Ln.begin(K_COLOUR);
+        launch_neighbour_colours(st, g->nnz, g->col_idx, col, (uint8_t *)W(p->off_ncol));
+        Ln.end(1, (double)g->nnz * 6);
+        ncol = (const uint8_t *)W(p->off_ncol);
+    }
+    // the skip for gathering a table of sets of size h
+    auto skip_for = [&](int h) {
+        AbsentSkip sk;
+        if (ncol) {
+            sk.ncol = ncol;
+            sk.smask = p->d_smask.at(h);
+        }
+        return sk;
+    };
     uint32_t *hist = (uint32_t *)W(p->off_hist);
     // the histogram of a leaf child with label `lab` (-1: all neighbours)
     auto hist_for = [&](int lab) -> uint32_t * {
@@ -917,7 +958,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                 if (vmid > v0) {
                     launch_gather_select(st, Ls, L, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps, Ch0,
                                          Chs0, p->d_ad[s.p], p->d_rm[s.h], col, out0, next_counter(), 4, nch,
-                                         vertex_group(nch), vstride(0, Chs0));
+                                         vertex_group(nch), vstride(0, Chs0), skip_for(s.p));
                     launch_leaf_chain(st, L, v0, vmid, p->split, g->row_ptr, B, k, out0, vstride(0, Chs0), Chs0, lc,
                                       next_counter());
                     nl += 2;
@@ -929,7 +970,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     launch_gather_select_chain(st, Ls, Lf, L, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp, Cps,
                                                Ch0, Chs0, p->d_ad[s.p], p->d_rm[s.h], col,
                                                out0 + (vmid - v0) * vstride(0, Chs0), vstride(0, Chs0), lt,
-                                               next_counter());
+                                               next_counter(), 4, skip_for(s.p));
                     nl++;
                 }
                 Ln.end(nl, chain_bytes(e_blk - (double)hv.edges, (double)(nv - nh)));
@@ -938,7 +979,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                     Ln.begin(K_HEAVY);
                     uint64_t *part = (uint64_t *)W(p->off_partial);
                     launch_gather_tasks(st, Ls, L, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                        next_counter(), 4, column_segments(R, Ls, p->col_chunks));
+                                        next_counter(), 4, column_segments(R, Ls, p->col_chunks), skip_for(s.p));
                     launch_gather_reduce(st, L, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                     launch_select_heavy(st, L, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch0, Chs0, Cps, p->d_rm[s.h], col,
                                         agg, out0);
@@ -1001,11 +1042,12 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         if (vmid > v0)
                             launch_gather_select(st, Ls, Lo, v0, vmid, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
                                                  Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col, out, next_counter(),
-                                                 nb, nch, vertex_group(nch));
+                                                 nb, nch, vertex_group(nch), 0, skip_for(s.p));
                         if (v1 > vmid)
                             launch_gather_select(st, Ls, Lo, vmid, v1, p->split, g->row_ptr, g->col_idx, X, B, k, Cp,
                                                  Cps, Ch, Chs, p->d_ad[s.p], p->d_rm[s.h], col,
-                                                 out + (vmid - v0) * B * Chs * Lo, next_counter(), nb);
+                                                 out + (vmid - v0) * B * Chs * Lo, next_counter(), nb, 1, 1, 0,
+                                                 skip_for(s.p));
                     };
                     int nl = 0, nb_tasks = 2;
                     if (tune) {
@@ -1031,7 +1073,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                         Ln.begin(K_HEAVY);
                         uint64_t *part = (uint64_t *)W(p->off_partial);
                         launch_gather_tasks(st, Ls, Lo, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part, false,
-                                            next_counter(), nb_tasks, column_segments(R, Ls, p->col_chunks));
+                                            next_counter(), nb_tasks, column_segments(R, Ls, p->col_chunks),
+                                            skip_for(s.p));
                         launch_gather_reduce(st, Lo, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part, R, agg);
                         launch_select_heavy(st, Lo, hv.h0, hv.h1, v0, sp.heavy_v, B, k, Ch, Chs, Cps, p->d_rm[s.h], col,
                                             agg, out);
@@ -1072,7 +1115,8 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 launch_gather_light(st, Ls, Lg, v0, v1, p->split, g->row_ptr, g->col_idx, X, R, agg,
                                                     gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
                                                     column_segments(R, Ls, p->col_chunks),
-                                                    vertex_group(column_segments(R, Ls, p->col_chunks)));
+                                                    vertex_group(column_segments(R, Ls, p->col_chunks)),
+                                                    skip_for(s.p));
                             Ln.end(1, light_bytes);
                             if (hv.t1 > hv.t0) {
                                 Ln.begin(K_HEAVY);
@@ -1088,7 +1132,7 @@ static cc_status launch_pass(Ctx *c, PlanInstance *p, char *ws, cudaStream_t st,
                                 else
                                     launch_gather_tasks(st, Ls, Lg, hv.t0, hv.t1, g->col_idx, sp.task_e, X, R, part,
                                                         gm == 4, gm == 5 ? nullptr : next_counter(), gm == 6 ? 2 : 4,
-                                                        column_segments(R, Ls, p->col_chunks));
+                                                        column_segments(R, Ls, p->col_chunks), skip_for(s.p));
                                 launch_gather_reduce(st, Lg, hv.h0, hv.h1, v0, hv.t0, sp.heavy_v, sp.heavy_tptr, part,
                                                      R, agg);
                                 Ln.end(2, heavy_bytes);

@@ -64,7 +64,8 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
                      const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
                      int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,
                      const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col,
-                     uint64_t *__restrict__ out, int64_t out_vs, unsigned long long *next, int nch, int G)
+                     uint64_t *__restrict__ out, int64_t out_vs, unsigned long long *next, int nch, int G,
+                     AbsentSkip sk)
 {
     const int lane = threadIdx.x & 31;
     const int R = B * Cps;
@@ -90,7 +91,7 @@ gather_select_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__res
                 Wide<Ld> acc[VPT];
 #pragma unroll
                 for (int q = 0; q < VPT; q++) wzero(acc[q]);
-                accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+                accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
                 scatter_sums<Ld, VPT>(orow, acc, base, b1, Cp, Cps, Chs, k, add_p, cv, pos, lane);
             }
         }
@@ -213,7 +214,7 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
                            const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int B, int k,
                            int Cp, int Cps, int Ch, int Chs, const uint16_t *__restrict__ add_p,
                            const uint16_t *__restrict__ rm_h, const uint8_t *__restrict__ col, uint64_t *out,
-                           int64_t out_vs, LeafChain chain, unsigned long long *next)
+                           int64_t out_vs, LeafChain chain, unsigned long long *next, AbsentSkip sk)
 {
     const int lane = threadIdx.x & 31;
     const int R = B * Cps;
@@ -233,7 +234,7 @@ gather_select_chain_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t 
                 Wide<Lf> acc[VPT];
 #pragma unroll
                 for (int q = 0; q < VPT; q++) wzero(acc[q]);
-                accumulate_rows<Ls, Lf, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+                accumulate_rows<Ls, Lf, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
                 scatter_sums<Lf, VPT>(orow, acc, base, R, Cp, Cps, Chs, k, add_p, cv, pos, lane);
             }
             leaf_steps<Ld, Lf>(v, v0, orow, Chs, chain, B, k, lane);
@@ -269,7 +270,7 @@ template <int Ls, int Ld>
 void gather_select_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                      const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
                      int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col, uint64_t *out,
-                     unsigned long long *next, int nch, int G, int64_t out_vs)
+                     unsigned long long *next, int nch, int G, int64_t out_vs, AbsentSkip sk)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
     auto kfn = nb == 4 ? gather_select_kernel<Ls, Ld, VPT, 4> : gather_select_kernel<Ls, Ld, VPT, 2>;
@@ -277,7 +278,7 @@ void gather_select_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int64_t sp
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(items, kWarps));
     note_launch("gather_select_kernel", Ls, Ld);
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
-                                   out_vs > 0 ? out_vs : (int64_t)B * Chs * Ld, next, nch, G);
+                                   out_vs > 0 ? out_vs : (int64_t)B * Chs * Ld, next, nch, G, sk);
 }
 
 }  // namespace
@@ -286,12 +287,12 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
                           const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                           const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next, int nb,
-                          int nch, int G, int64_t out_vs)
+                          int nch, int G, int64_t out_vs, AbsentSkip sk)
 {
     if (v1 <= v0) return;
     nch = std::max(1, std::min(nch, 64));
     G = std::max(1, G);
-#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next, nch, G, out_vs)
+#define CC_GS(a, b) if (Ls == a && Ld == b) return gather_select_t<a, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, next, nch, G, out_vs, sk)
     CC_GS(1, 1); CC_GS(1, 2); CC_GS(1, 3); CC_GS(1, 4);
     CC_GS(2, 1); CC_GS(2, 2); CC_GS(2, 3); CC_GS(2, 4);
     CC_GS(3, 1); CC_GS(3, 2); CC_GS(3, 3); CC_GS(3, 4);
@@ -306,14 +307,14 @@ void gather_select_chain_t(cudaStream_t st, int nb, int64_t v0, int64_t v1, int6
                            const int32_t *ci, const uint64_t *X, int B, int k, int64_t Cp, int64_t Cps, int64_t Ch,
                            int64_t Chs, const uint16_t *add_p, const uint16_t *rm_h, const uint8_t *col,
                            uint64_t *out, int64_t out_vs, const LeafChain &chain,
-                           unsigned long long *next)
+                           unsigned long long *next, AbsentSkip sk)
 {
     constexpr int VPT = Lf <= 2 ? 4 : 2;
     auto kfn = nb == 4 ? gather_select_chain_kernel<Ls, Lf, Ld, VPT, 4> : gather_select_chain_kernel<Ls, Lf, Ld, VPT, 2>;
     const unsigned g = std::min<unsigned>(persistent_ctas(kfn), grid_for(v1 - v0, kWarps));
     note_launch("gather_select_chain_kernel", Ls, Lf, Ld);
     kfn<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out,
-                                   out_vs, chain, next);
+                                   out_vs, chain, next, sk);
 }
 
 }  // namespace
@@ -322,12 +323,12 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t
                                 const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
-                                const LeafChain &chain, unsigned long long *next, int nb)
+                                const LeafChain &chain, unsigned long long *next, int nb, AbsentSkip sk)
 {
     if (v1 <= v0) return;
     // Lf is Ld or Ld - 1 (the fused step's own width, at most one limb narrower)
     if (Lf < Ld - 1 || Lf > Ld || Lf < 1) Lf = Ld;
-#define CC_GC(a, f, b) if (Ls == a && Lf == f && Ld == b) return gather_select_chain_t<a, f, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, next)
+#define CC_GC(a, f, b) if (Ls == a && Lf == f && Ld == b) return gather_select_chain_t<a, f, b>(st, nb, v0, v1, split, row_ptr, col_idx, X, B, k, Cp, Cps, Ch, Chs, add_p, rm_h, col, out, out_vs, chain, next, sk)
 #define CC_GC_LS(a) CC_GC(a, 1, 1); CC_GC(a, 1, 2); CC_GC(a, 2, 2); CC_GC(a, 2, 3); CC_GC(a, 3, 3); CC_GC(a, 3, 4); CC_GC(a, 4, 4)
     CC_GC_LS(1); CC_GC_LS(2); CC_GC_LS(3); CC_GC_LS(4);
 #undef CC_GC_LS

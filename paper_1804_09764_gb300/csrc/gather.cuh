@@ -25,23 +25,54 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// One batch of NB neighbours (ids in lanes t .. t + NB - 1 of myu) of the row
+// Neighbour ids travel through the warp with the neighbour's colour in bits
+// 27..30 when absent entries are skipped (AbsentSkip); kIdBits masks the id.
+constexpr uint32_t kIdBits = (1u << 27) - 1;
+
+// Per-lane skip state of one sweep: m[q] = the colour mask of value base +
+// q * 32 + lane (all colours without skipping, 0 past the row), idm = the id
+// bits of a broadcast neighbour word.
+template <int VPT>
+struct LaneMask {
+    uint32_t m[VPT];
+    uint32_t idm;
+    __device__ __forceinline__ void init(const AbsentSkip &sk, int64_t R, int64_t base, int lane)
+    {
+        idm = sk.ncol ? kIdBits : 0x7fffffffu;
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const int64_t c = base + q * 32 + lane;
+            m[q] = c < R ? (sk.ncol ? (uint32_t)__ldg(sk.smask + c) : 0xffffu) : 0u;
+        }
+    }
+    // this lane's word for list entry e (lane < cnt): the id, with the colour above it
+    __device__ __forceinline__ int32_t word(const AbsentSkip &sk, const int32_t *__restrict__ col_idx, int64_t e) const
+    {
+        int32_t w = __ldg(col_idx + e);
+        if (sk.ncol) w |= (int32_t)((uint32_t)__ldg(sk.ncol + e) << 27);
+        return w;
+    }
+};
+
+// One batch of NB neighbours (words in lanes t .. t + NB - 1 of myu) of the row
 // sums below: every load of the batch is issued before any is added, NB * VPT
 // loads in flight per lane.  xl points at value base + lane of row 0; row u
-// starts rb * u bytes further; ok[q]: value base + q * 32 + lane is in the row.
+// starts rb * u bytes further; a value is loaded only where its colour mask
+// holds the neighbour's colour (the others are zero, AbsentSkip).
 template <int Ls, int Ld, int VPT, int NB>
 __device__ __forceinline__ void sum_batch(RowSum<Ls, Ld> (&s)[VPT], const char *xl, uint32_t rb, int32_t myu, int t,
-                                          const bool (&ok)[VPT])
+                                          const LaneMask<VPT> &lm)
 {
     using S = RowSum<Ls, Ld>;
     Wide<S::N> x[NB][VPT];
 #pragma unroll
     for (int j = 0; j < NB; j++) {
-        const uint32_t u = (uint32_t)__shfl_sync(0xffffffffu, myu, t + j);
-        const uint64_t *row = reinterpret_cast<const uint64_t *>(xl + (uint64_t)u * rb);
+        const uint32_t w = (uint32_t)__shfl_sync(0xffffffffu, myu, t + j);
+        const uint32_t bit = 1u << (w >> 27);
+        const uint64_t *row = reinterpret_cast<const uint64_t *>(xl + (uint64_t)(w & lm.idm) * rb);
 #pragma unroll
         for (int q = 0; q < VPT; q++) {
-            if (ok[q])
+            if (lm.m[q] & bit)
                 x[j][q] = S::load(row + q * 32 * Ls);
             else
                 wzero(x[j][q]);
@@ -62,23 +93,22 @@ __device__ __forceinline__ void sum_batch(RowSum<Ls, Ld> (&s)[VPT], const char *
 template <int Ls, int Ld, int VPT, int NB>
 __device__ __forceinline__ void accumulate_rows_counted(const int32_t *__restrict__ col_idx, int64_t e0,
                                                         int64_t e1, const uint64_t *__restrict__ X, int64_t R,
-                                                        int64_t base, Wide<Ld> (&acc)[VPT], int lane)
+                                                        int64_t base, Wide<Ld> (&acc)[VPT], int lane,
+                                                        const AbsentSkip &sk)
 {
     RowSum<Ls, Ld> s[VPT];
-    bool ok[VPT];
+    LaneMask<VPT> lm;
+    lm.init(sk, R, base, lane);
 #pragma unroll
-    for (int q = 0; q < VPT; q++) {
-        s[q].zero();
-        ok[q] = base + q * 32 + lane < R;
-    }
+    for (int q = 0; q < VPT; q++) s[q].zero();
     const char *xl = reinterpret_cast<const char *>(X + (base + lane) * Ls);
     const uint32_t rb = (uint32_t)(R * Ls * 8);
     for (int64_t e = e0; e < e1; e += 32) {
         const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
-        const int32_t myu = lane < cnt ? __ldg(col_idx + e + lane) : 0;
+        const int32_t myu = lane < cnt ? lm.word(sk, col_idx, e + lane) : 0;
         const int nfull = cnt - cnt % NB;
-        for (int t = 0; t < nfull; t += NB) sum_batch<Ls, Ld, VPT, NB>(s, xl, rb, myu, t, ok);
-        for (int t = nfull; t < cnt; t++) sum_batch<Ls, Ld, VPT, 1>(s, xl, rb, myu, t, ok);
+        for (int t = 0; t < nfull; t += NB) sum_batch<Ls, Ld, VPT, NB>(s, xl, rb, myu, t, lm);
+        for (int t = nfull; t < cnt; t++) sum_batch<Ls, Ld, VPT, 1>(s, xl, rb, myu, t, lm);
     }
 #pragma unroll
     for (int q = 0; q < VPT; q++) acc[q] = s[q].wide();
@@ -87,26 +117,30 @@ __device__ __forceinline__ void accumulate_rows_counted(const int32_t *__restric
 // acc[q] += X[u][base + q*32 + lane] over the neighbours u of col_idx[e0, e1)
 // with full Ld-limb adds: neighbour ids are fetched 32 at a time and broadcast
 // with shuffles, and NB neighbours' values are loaded before any is added
-// (NB * VPT loads in flight per lane).
+// (NB * VPT loads in flight per lane).  Absent entries are skipped as above.
 template <int Ls, int Ld, int VPT, int NB>
 __device__ __forceinline__ void accumulate_rows_limbwise(const int32_t *__restrict__ col_idx, int64_t e0,
                                                          int64_t e1, const uint64_t *__restrict__ X, int64_t R,
-                                                         int64_t base, Wide<Ld> (&acc)[VPT], int lane)
+                                                         int64_t base, Wide<Ld> (&acc)[VPT], int lane,
+                                                         const AbsentSkip &sk)
 {
+    LaneMask<VPT> lm;
+    lm.init(sk, R, base, lane);
     for (int64_t e = e0; e < e1; e += 32) {
         const int cnt = (e1 - e < 32) ? (int)(e1 - e) : 32;
-        const int32_t myu = lane < cnt ? col_idx[e + lane] : 0;
+        const int32_t myu = lane < cnt ? lm.word(sk, col_idx, e + lane) : 0;
         int t = 0;
         for (; t + NB <= cnt; t += NB) {
             Wide<Ld> x[NB][VPT];
 #pragma unroll
             for (int j = 0; j < NB; j++) {
-                const int64_t u = __shfl_sync(0xffffffffu, myu, t + j);
-                const uint64_t *row = X + u * R * Ls;
+                const uint32_t w = (uint32_t)__shfl_sync(0xffffffffu, myu, t + j);
+                const uint32_t bit = 1u << (w >> 27);
+                const uint64_t *row = X + (int64_t)(w & lm.idm) * R * Ls;
 #pragma unroll
                 for (int q = 0; q < VPT; q++) {
                     const int64_t c = base + q * 32 + lane;
-                    if (c < R)
+                    if (lm.m[q] & bit)
                         x[j][q] = wload<Ls, Ld>(row + c * Ls);
                     else
                         wzero(x[j][q]);
@@ -118,12 +152,13 @@ __device__ __forceinline__ void accumulate_rows_limbwise(const int32_t *__restri
                 for (int q = 0; q < VPT; q++) wadd(acc[q], x[j][q]);
         }
         for (; t < cnt; t++) {
-            const int64_t u = __shfl_sync(0xffffffffu, myu, t);
-            const uint64_t *row = X + u * R * Ls;
+            const uint32_t w = (uint32_t)__shfl_sync(0xffffffffu, myu, t);
+            const uint32_t bit = 1u << (w >> 27);
+            const uint64_t *row = X + (int64_t)(w & lm.idm) * R * Ls;
 #pragma unroll
             for (int q = 0; q < VPT; q++) {
                 const int64_t c = base + q * 32 + lane;
-                if (c < R) wadd(acc[q], wload<Ls, Ld>(row + c * Ls));
+                if (lm.m[q] & bit) wadd(acc[q], wload<Ls, Ld>(row + c * Ls));
             }
         }
     }
@@ -138,12 +173,12 @@ __device__ __forceinline__ void accumulate_rows_limbwise(const int32_t *__restri
 template <int Ls, int Ld, int VPT, int NB>
 __device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
                                                 const uint64_t *__restrict__ X, int64_t R, int64_t base,
-                                                Wide<Ld> (&acc)[VPT], int lane)
+                                                Wide<Ld> (&acc)[VPT], int lane, const AbsentSkip &sk)
 {
     if constexpr (Ls == 1)
-        accumulate_rows_counted<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+        accumulate_rows_counted<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
     else
-        accumulate_rows_limbwise<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+        accumulate_rows_limbwise<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
 }
 
 // Sum rows X[u] over the neighbour sub-list col_idx[e0, e1) into out_row.
@@ -153,7 +188,7 @@ __device__ __forceinline__ void accumulate_rows(const int32_t *__restrict__ col_
 template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
                                            const uint64_t *__restrict__ X, int64_t R,
-                                           uint64_t *__restrict__ out_row, int lane)
+                                           uint64_t *__restrict__ out_row, int lane, const AbsentSkip &sk)
 {
     for (int64_t base = 0; base < R; base += 32 * VPT) {
         Wide<Ld> acc[VPT];
@@ -162,7 +197,7 @@ __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, 
         if (PF && base == 0 && R > 32 * VPT && (R * Ls) % 2 == 0)
             for (int64_t e = e0 + lane; e < e1; e += 32)
                 prefetch_l2(X + (int64_t)col_idx[e] * R * Ls, (uint32_t)(R * Ls * 8));
-        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
 #pragma unroll
         for (int q = 0; q < VPT; q++) {
             const int64_t c = base + q * 32 + lane;
@@ -176,13 +211,13 @@ __device__ __forceinline__ void gather_row(const int32_t *__restrict__ col_idx, 
 template <int Ls, int Ld, int VPT, int NB>
 __device__ __forceinline__ void gather_row_range(const int32_t *__restrict__ col_idx, int64_t e0, int64_t e1,
                                                  const uint64_t *__restrict__ X, int64_t R, int64_t b0, int64_t b1,
-                                                 uint64_t *__restrict__ out_row, int lane)
+                                                 uint64_t *__restrict__ out_row, int lane, const AbsentSkip &sk)
 {
     for (int64_t base = b0; base < b1; base += 32 * VPT) {
         Wide<Ld> acc[VPT];
 #pragma unroll
         for (int q = 0; q < VPT; q++) wzero(acc[q]);
-        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane);
+        accumulate_rows<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, base, acc, lane, sk);
 #pragma unroll
         for (int q = 0; q < VPT; q++) {
             const int64_t c = base + q * 32 + lane;

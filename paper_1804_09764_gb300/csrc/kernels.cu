@@ -535,7 +535,7 @@ template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__restrict__ row_ptr,
                     const int32_t *__restrict__ col_idx, const uint64_t *__restrict__ X, int64_t R,
-                    uint64_t *__restrict__ agg, unsigned long long *next, int nch, int G)
+                    uint64_t *__restrict__ agg, unsigned long long *next, int nch, int G, AbsentSkip sk)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!next) {
@@ -543,7 +543,7 @@ gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__rest
         if (v >= v1) return;
         const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
         if (e1 - e0 <= split)  // heavy vertices are summed from their tasks
-            gather_row<Ls, Ld, VPT, PF, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+            gather_row<Ls, Ld, VPT, PF, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane, sk);
         return;
     }
     const int64_t ngrp = (v1 - v0 + G - 1) / G, cw = segment_width<VPT>(R, nch);
@@ -558,10 +558,10 @@ gather_light_kernel(int64_t v0, int64_t v1, int64_t split, const int64_t *__rest
             const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
             if (e1 - e0 > split) continue;
             if (nch == 1)
-                gather_row<Ls, Ld, VPT, PF, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane);
+                gather_row<Ls, Ld, VPT, PF, NB>(col_idx, e0, e1, X, R, agg + (v - v0) * R * Ld, lane, sk);
             else
                 gather_row_range<Ls, Ld, VPT, NB>(col_idx, e0, e1, X, R, seg * cw, min(R, (seg + 1) * cw),
-                                                  agg + (v - v0) * R * Ld, lane);
+                                                  agg + (v - v0) * R * Ld, lane, sk);
         }
     }
 }
@@ -574,14 +574,14 @@ template <int Ls, int Ld, int VPT, bool PF = false, int NB = 2>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
                     const int64_t *__restrict__ task_e, const uint64_t *__restrict__ X, int64_t R,
-                    uint64_t *__restrict__ partial, unsigned long long *next, int nch)
+                    uint64_t *__restrict__ partial, unsigned long long *next, int nch, AbsentSkip sk)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!next) {
         const int64_t t = t0 + blockIdx.x * (int64_t)kWarps + warp;
         if (t < t1)
             gather_row<Ls, Ld, VPT, PF, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R,
-                                            partial + (t - t0) * R * Ld, lane);
+                                            partial + (t - t0) * R * Ld, lane, sk);
         return;
     }
     const int64_t nt = t1 - t0, cw = segment_width<VPT>(R, nch);
@@ -593,10 +593,10 @@ gather_tasks_kernel(int64_t t0, int64_t t1, const int32_t *__restrict__ col_idx,
         const int64_t seg = i / nt, t = t0 + (i - seg * nt);
         if (nch == 1)
             gather_row<Ls, Ld, VPT, PF, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R,
-                                            partial + (t - t0) * R * Ld, lane);
+                                            partial + (t - t0) * R * Ld, lane, sk);
         else
             gather_row_range<Ls, Ld, VPT, NB>(col_idx, task_e[2 * t], task_e[2 * t + 1], X, R, seg * cw,
-                                              min(R, (seg + 1) * cw), partial + (t - t0) * R * Ld, lane);
+                                              min(R, (seg + 1) * cw), partial + (t - t0) * R * Ld, lane, sk);
     }
 }
 
@@ -855,6 +855,14 @@ __global__ void max_sum_kernel(int64_t n, const double *__restrict__ x, double *
     }
 }
 
+// the colour of every list entry's neighbour in the pass's one colouring
+__global__ void neighbour_colours_kernel(int64_t nnz, const int32_t *__restrict__ col_idx,
+                                         const uint8_t *__restrict__ col, uint8_t *__restrict__ ncol)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        ncol[e] = col[col_idx[e]];
+}
+
 // labelled templates: rows of vertices whose label is not `want` become zero
 __global__ void mask_rows_kernel(int64_t nv, int64_t row_words, const uint8_t *__restrict__ labels, int want,
                                  uint64_t *__restrict__ rows)
@@ -895,7 +903,7 @@ __global__ void permute_lists_kernel(int64_t n_act, int64_t n, const int64_t *__
 template <int Ls, int Ld>
 void gather_light_t(cudaStream_t st, bool pf, int nb, int64_t v0, int64_t v1, int64_t split, const int64_t *rp,
                     const int32_t *ci, const uint64_t *X, int64_t R, uint64_t *agg, unsigned long long *next, int nch,
-                    int G)
+                    int G, AbsentSkip sk)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
     auto k = pf ? gather_light_kernel<Ls, Ld, VPT, true, 2>
@@ -904,12 +912,13 @@ void gather_light_t(cudaStream_t st, bool pf, int nb, int64_t v0, int64_t v1, in
     const int64_t items = (v1 - v0 + G - 1) / G * nch;
     const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(items, kWarps)) : grid_for(v1 - v0, kWarps);
     note_launch("gather_light_kernel", Ls, Ld);
-    k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next, nch, G);
+    k<<<g, kWarps * 32, 0, st>>>(v0, v1, split, rp, ci, X, R, agg, next, nch, G, sk);
 }
 
 template <int Ls, int Ld>
 void gather_tasks_t(cudaStream_t st, bool pf, int nb, int64_t t0, int64_t t1, const int32_t *ci, const int64_t *te,
-                    const uint64_t *X, int64_t R, uint64_t *partial, unsigned long long *next, int nch)
+                    const uint64_t *X, int64_t R, uint64_t *partial, unsigned long long *next, int nch,
+                    AbsentSkip sk)
 {
     constexpr int VPT = Ld <= 2 ? 4 : 2;
     auto k = pf ? gather_tasks_kernel<Ls, Ld, VPT, true, 2>
@@ -918,7 +927,7 @@ void gather_tasks_t(cudaStream_t st, bool pf, int nb, int64_t t0, int64_t t1, co
     const int64_t items = (t1 - t0) * nch;
     const unsigned g = next ? std::min<unsigned>(persistent_ctas(k), grid_for(items, kWarps)) : grid_for(t1 - t0, kWarps);
     note_launch("gather_tasks_kernel", Ls, Ld);
-    k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next, nch);
+    k<<<g, kWarps * 32, 0, st>>>(t0, t1, ci, te, X, R, partial, next, nch, sk);
 }
 
 }  // namespace
@@ -962,6 +971,14 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
                                                                   hist);
 }
 
+void launch_neighbour_colours(cudaStream_t st, int64_t nnz, const int32_t *col_idx, const uint8_t *col,
+                              uint8_t *ncol)
+{
+    if (nnz <= 0) return;
+    note_launch("neighbour_colours_kernel");
+    neighbour_colours_kernel<<<grid_stride_ctas(nnz, 256), 256, 0, st>>>(nnz, col_idx, col, ncol);
+}
+
 void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint8_t *labels, int want, uint64_t *rows)
 {
     if (nv <= 0 || row_words <= 0) return;
@@ -970,12 +987,13 @@ void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint
 
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int64_t R,
-                         uint64_t *agg, bool prefetch, unsigned long long *next, int nb, int nch, int G)
+                         uint64_t *agg, bool prefetch, unsigned long long *next, int nb, int nch, int G,
+                         AbsentSkip sk)
 {
     if (v1 <= v0) return;
     nch = std::max(1, std::min(nch, 64));
     G = std::max(1, G);
-#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, nb, v0, v1, split, row_ptr, col_idx, X, R, agg, next, nch, G)
+#define CC_GL(a, b) if (Ls == a && Ld == b) return gather_light_t<a, b>(st, prefetch, nb, v0, v1, split, row_ptr, col_idx, X, R, agg, next, nch, G, sk)
     CC_GL(1, 1); CC_GL(1, 2); CC_GL(1, 3); CC_GL(1, 4);
     CC_GL(2, 1); CC_GL(2, 2); CC_GL(2, 3); CC_GL(2, 4);
     CC_GL(3, 1); CC_GL(3, 2); CC_GL(3, 3); CC_GL(3, 4);
@@ -1138,11 +1156,11 @@ void launch_gather_tasks_bulk(cudaStream_t st, int Ls, int Ld, int64_t t0, int64
 
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1, const int32_t *col_idx,
                          const int64_t *task_e, const uint64_t *X, int64_t R, uint64_t *partial, bool prefetch,
-                         unsigned long long *next, int nb, int nch)
+                         unsigned long long *next, int nb, int nch, AbsentSkip sk)
 {
     if (t1 <= t0) return;
     nch = std::max(1, std::min(nch, 64));
-#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, nb, t0, t1, col_idx, task_e, X, R, partial, next, nch)
+#define CC_GT(a, b) if (Ls == a && Ld == b) return gather_tasks_t<a, b>(st, prefetch, nb, t0, t1, col_idx, task_e, X, R, partial, next, nch, sk)
     CC_GT(1, 1); CC_GT(1, 2); CC_GT(1, 3); CC_GT(1, 4);
     CC_GT(2, 1); CC_GT(2, 2); CC_GT(2, 3); CC_GT(2, 4);
     CC_GT(3, 1); CC_GT(3, 2); CC_GT(3, 3); CC_GT(3, 4);

@@ -41,6 +41,23 @@ void launch_hist(cudaStream_t st, int64_t v0, int64_t v1, int B, int k, const in
 // labelled templates: rows[v][0 .. row_words) = 0 for v in [0, nv) with labels[v] != want
 void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint8_t *labels, int want, uint64_t *rows);
 
+// Entries that a gathered table holds as zero by construction: M(u, T, S) = 0
+// when col(u) is not in S (the root of T is mapped to u, Eq. 1), so in a pass
+// of one colouring (B = 1, row = the C(k, |T|) colex columns) a gather need not
+// load them.  ncol[e] = col(col_idx[e]) (neighbour colours of the pass, one
+// byte per list entry, written by launch_neighbour_colours); smask[s] = the
+// colour set of column s as a bit mask (0 for the padding column).  With ncol
+// == nullptr every entry is loaded.  Needs k <= 16 and ids below 2^27 (the
+// colour travels in bits 27..30 of the id broadcast to the warp).
+struct AbsentSkip {
+    const uint8_t *ncol = nullptr;
+    const uint16_t *smask = nullptr;
+};
+
+// ncol[e] = col[col_idx[e]] for e in [0, nnz) (one colouring per pass)
+void launch_neighbour_colours(cudaStream_t st, int64_t nnz, const int32_t *col_idx, const uint8_t *col,
+                              uint8_t *ncol);
+
 // agg[v - v0] = sum_{u in N(v)} X[u]  over rows of R values; light vertices only
 // (deg <= split), heavy ones go through tasks + reduce.
 // prefetch: also request each neighbour row whole into L2 (cp.async.bulk.prefetch)
@@ -52,7 +69,7 @@ void launch_mask_rows(cudaStream_t st, int64_t nv, int64_t row_words, const uint
 void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1, int64_t split,
                          const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X,
                          int64_t R, uint64_t *agg, bool prefetch = false, unsigned long long *next = nullptr,
-                         int nb = 4, int nch = 1, int G = 1);
+                         int nb = 4, int nch = 1, int G = 1, AbsentSkip sk = {});
 
 // tasks [t0, t1): neighbour sub-lists (task_v, task_e0, task_e1); each writes partial[t - t0]
 // nch > 1 (with next): the row is split into nch column segments run
@@ -60,7 +77,7 @@ void launch_gather_light(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v1
 void launch_gather_tasks(cudaStream_t st, int Ls, int Ld, int64_t t0, int64_t t1,
                          const int32_t *col_idx, const int64_t *task_e, const uint64_t *X,
                          int64_t R, uint64_t *partial, bool prefetch = false, unsigned long long *next = nullptr,
-                         int nb = 4, int nch = 1);
+                         int nb = 4, int nch = 1, AbsentSkip sk = {});
 
 // column segments for rows of R values of Ls limbs: requested > 0 as given
 // (<= 64); 0: one 128-value warp sweep per segment, at most 16
@@ -135,7 +152,7 @@ void launch_gather_select(cudaStream_t st, int Ls, int Ld, int64_t v0, int64_t v
                           const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                           int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                           const uint16_t *rm_h, const uint8_t *col, uint64_t *out, unsigned long long *next,
-                          int nb = 4, int nch = 1, int G = 1, int64_t out_vs = 0);
+                          int nb = 4, int nch = 1, int G = 1, int64_t out_vs = 0, AbsentSkip sk = {});
 // (nch, G as for launch_gather_light; out_vs: 64-bit words between the output
 // rows of consecutive vertices, 0 = B * Chs * Ld)
 // Chain version: after the fused step the same warp runs the chain's following
@@ -162,7 +179,8 @@ void launch_gather_select_chain(cudaStream_t st, int Ls, int Lf, int Ld, int64_t
                                 const int64_t *row_ptr, const int32_t *col_idx, const uint64_t *X, int B, int k,
                                 int64_t Cp, int64_t Cps, int64_t Ch, int64_t Chs, const uint16_t *add_p,
                                 const uint16_t *rm_h, const uint8_t *col, uint64_t *out, int64_t out_vs,
-                                const LeafChain &chain, unsigned long long *next, int nb = 4);
+                                const LeafChain &chain, unsigned long long *next, int nb = 4,
+                                AbsentSkip sk = {});
 
 // The chain's p = 1 steps for the light vertices of [v0, v1) whose first-step
 // rows are at out0 + (v - v0) * out_vs (written by launch_gather_select).

@@ -137,6 +137,7 @@ struct PlanInstance {
     std::vector<uint16_t *> d_ad;               // [p] (fused gather + select steps)
     std::map<std::pair<int, int>, uint32_t *> d_pairs;
     std::map<int, uint16_t *> d_elig;           // [h]: per colour, the ranks of the h-sets holding it
+    std::vector<uint16_t *> d_smask;            // [h]: colour mask of each column (AbsentSkip), 0 padding
     // workspace layout (offsets from ws base)
     uint64_t ws_bytes = 0;
     // workspace of the same plan with every table kept for the whole pass, with
@@ -144,6 +145,8 @@ struct PlanInstance {
     uint64_t ws_no_reuse = 0, ws_no_blocks = 0, ws_naive = 0;
     uint64_t off_col = 0, off_hist = 0, off_act[2] = {0, 0}, off_agg = 0, off_partial = 0, off_root = 0,
              off_scratch = 0, off_totals = 0, off_params = 0, off_err = 0, off_ctr = 0;
+    uint64_t off_ncol = ~0ull;        // neighbour colours of the pass (AbsentSkip), ~0: whole rows
+    bool absent_skip = false;         // the plan may skip absent entries (batch 1 decides)
     std::vector<uint64_t> off_table;  // per chain (materialised), ~0 for root
     // analytic figures
     double updates = 0, gather_bytes = 0, alg_bytes = 0, pairs = 0, limb_products = 0;
