@@ -101,3 +101,12 @@ def test_sixteen_colours():
     g = gg.disjoint_union(gg.er_graph(300, 6, seed=5), gg.star_graph(40))
     e = gg.prufer_tree(16, seed=4)
     _check(g, 16, e, 0, 9, 1, split_threshold=16)
+
+
+def test_cuda_graph_replay_and_autotuner():
+    # the pass captured once and replayed for every colouring: the neighbour
+    # colours are rewritten inside the replay; the autotuner times every
+    # gather variant (those that read whole rows and those that skip)
+    g = gg.rmat_graph(11, seed=47)
+    k, e = gg.template_edges("tree12")
+    _check(g, k, e, 1, 31, 3, use_cuda_graph=1, autotune=1, split_threshold=40)
